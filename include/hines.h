@@ -1,0 +1,216 @@
+/*
+ * libhines -- batched direct solver for Hines matrices on one GB300 GPU.
+ *
+ * A Hines matrix (Huber, "Efficient Tree Solver for Hines Matrices on the
+ * GPU", Sections 1-2) is the symmetric, strictly diagonally dominant matrix of
+ * the implicit-Euler finite-volume discretisation of the cable equation on a
+ * neuron's dendritic tree.  For one cell with N compartments:
+ *
+ *     A[i][i] = d[i],   A[i][p[i]] = A[p[i]][i] = u[i]   (i > 0),
+ *
+ * with the parent array p in Hines numbering: p[0] = -1 and 0 <= p[i] < i
+ * (Section 2).  u[i] is the coupling of compartment i to its parent; u[0] is
+ * never read.  The solve is the Hines algorithm (Section 2, Listing 2): one
+ * leaf-to-root elimination and one root-to-leaf substitution, O(N).
+ *
+ * Layout ("natural layout").  A batch of n_cells cells is stored with the
+ * cells concatenated in the order they were given to hines_plan_create; cell c
+ * occupies [off[c], off[c+1]) (see hines_plan_layout) and its parent indices
+ * are cell-local.  All per-compartment device arrays use this layout.
+ *
+ * Ownership.  Device arrays passed to the solve calls belong to the caller.
+ * The plan owns its device metadata and a device workspace; it is created
+ * on the device that is current at hines_plan_create and every call must be
+ * made with that device current.
+ *
+ * Asynchrony.  Calls that take a stream only enqueue work on it and return;
+ * argument errors are returned synchronously, before anything is enqueued.
+ * Calls that share a plan must be ordered on one stream (they share the
+ * plan's workspace).  Nothing is allocated inside the solve calls.
+ *
+ * Errors.  Every entry point returns a hines_status; hines_status_string
+ * gives its text.  Device-side errors raise the plan's status word, read with
+ * hines_plan_status.
+ */
+#ifndef HINES_H
+#define HINES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t); NULL is the legacy default stream. */
+typedef struct CUstream_st *hines_stream_t;
+
+/* Opaque plan handle; owned by the library, released by hines_plan_destroy. */
+typedef struct hines_plan_s *hines_plan_t;
+
+typedef enum {
+  HINES_OK = 0,
+  HINES_ERR_INVALID_ARG = 1,     /* null pointer, negative size, bad dtype or option, host-only plan */
+  HINES_ERR_NOT_HINES_ORDER = 2, /* a cell violates p[0] = -1, 0 <= p[i] < i */
+  HINES_ERR_OOM = 3,             /* host or device allocation failed (plan creation only) */
+  HINES_ERR_CUDA = 4,            /* a CUDA runtime call failed */
+  HINES_ERR_TIMEOUT = 5,         /* a bounded device wait ran out (status word) */
+  HINES_WARN_REFINE = 6,         /* iterative refinement did not contract in some cell (status word) */
+  HINES_ERR_DEVICE = 7           /* the plan was created on another device than the current one */
+} hines_status;
+
+/* Element types of the solve arrays. */
+enum { HINES_F64 = 0, HINES_F32 = 1 };
+
+/* Plan options; pass NULL for the defaults (all zero). */
+typedef struct {
+  int32_t host_only;       /* 1: build the host-side plan only (no CUDA calls); it can be
+                              inspected with hines_plan_info / hines_plan_export but not solved */
+  int32_t split_branches;  /* 1: split branches longer than their level's mean (Section 6) */
+  int32_t cta_threads;     /* threads per CTA of the level-synchronous kernels (0: 256) */
+  int32_t reserved[5];     /* must be zero */
+} hines_plan_opts;
+
+/* Plan summary. */
+typedef struct {
+  int32_t n_cells;
+  int32_t max_levels;       /* deepest branch dependency tree (levels of Section 3) */
+  int64_t n_unknowns;       /* total compartments */
+  int64_t n_branches;       /* unbranched runs after optional splitting */
+  int64_t workspace_bytes;  /* device workspace owned by the plan */
+  int64_t metadata_bytes;   /* device metadata owned by the plan */
+} hines_plan_info_t;
+
+/*
+ * Build a plan for a batch of cells (host, once per morphology; Section 4:
+ * the distribution is computed once during setup).
+ *   n_cells  >= 0
+ *   ncomp    host int32[n_cells], compartments per cell (each >= 0)
+ *   parent   host int32[sum ncomp], cell-local parent arrays, concatenated
+ *   opts     NULL or options
+ * Validates every cell (HINES_ERR_NOT_HINES_ORDER names no cell; use a
+ * per-cell check on the host to find it), decomposes each tree into branches
+ * (maximal unbranched runs: compartment i starts a branch when i = 0,
+ * p[i] != i-1, or p[i] has two or more children), assigns levels (number of
+ * ancestor branches), orders the branches of every level by length
+ * (descending, ties by branch index; Section 4, Fig. 4.1), and uploads the
+ * metadata and a workspace to the current device.  On success *out receives
+ * the plan; on failure *out is NULL.
+ */
+hines_status hines_plan_create(hines_plan_t *out, int32_t n_cells, const int32_t *ncomp, const int32_t *parent,
+                               const hines_plan_opts *opts);
+
+/* Release a plan (NULL is a no-op).  Synchronises the plan's device. */
+hines_status hines_plan_destroy(hines_plan_t plan);
+
+/* Host int64[n_cells + 1]: offset of each cell in the natural layout. */
+hines_status hines_plan_layout(hines_plan_t plan, int64_t *cell_offsets);
+
+/* Fill *info with the plan's sizes. */
+hines_status hines_plan_info(hines_plan_t plan, hines_plan_info_t *info);
+
+/*
+ * Copy the planner's branch decomposition to host arrays (all int64 so that
+ * one call serves any batch size; every pointer may be NULL to skip it):
+ *   first[nb], len[nb], parent_branch[nb], level[nb], cell[nb]  per branch,
+ *        branches numbered cell by cell in order of their first compartment;
+ *        first is the natural-layout index of the proximal compartment,
+ *        parent_branch is -1 for a cell's root branch
+ *   order[nb]  the processing order: cell by cell, level by level from 0,
+ *        within a level by length descending then branch index
+ * nb = info.n_branches.
+ */
+hines_status hines_plan_export(hines_plan_t plan, int64_t *first, int64_t *len, int64_t *parent_branch,
+                               int64_t *level, int64_t *cell, int64_t *order);
+
+/*
+ * Solve A x = b for every cell (Section 2, Listing 2), in place.
+ *   dtype   HINES_F64 (arithmetic in FP64) or HINES_F32 (arithmetic in FP32)
+ *   d       device [n_unknowns] diagonal, not modified
+ *   u       device [n_unknowns] parent couplings, not modified (u[first of cell] unused)
+ *   b_inout device [n_unknowns] right-hand side on entry, solution x on return
+ * Stream-ordered; uses the plan's workspace.
+ */
+hines_status hines_solve(hines_plan_t plan, int32_t dtype, const void *d, const void *u, void *b_inout,
+                         hines_stream_t stream);
+
+/*
+ * Mixed-precision solve: elimination in FP32 on FP32 inputs, then
+ * refine_steps (0..4) steps of iterative refinement whose residual
+ * r = b - A x and correction x += A^{-1} r are carried in FP64 (A and b are
+ * the FP32 inputs widened exactly to FP64).  No paper counterpart (Section 2
+ * gives the FP64 algorithm only).
+ *   d, u, b      device float[n_unknowns], not modified
+ *   x_out        device double[n_unknowns], the solution
+ *   cell_relres  device double[n_cells] or NULL: per cell the scaled residual
+ *                ||b - A x||_inf / (||A||_inf ||x||_inf) of the returned x, in FP64
+ * If a refinement step grows the correction in some cell the plan's status
+ * word receives HINES_WARN_REFINE.
+ */
+hines_status hines_solve_refine(hines_plan_t plan, const float *d, const float *u, const float *b, double *x_out,
+                                int32_t refine_steps, double *cell_relres, hines_stream_t stream);
+
+/*
+ * One implicit-Euler step of a passive cable for every cell: the system of
+ * Section 1 (finite volume, implicit Euler) is rebuilt from V and solved,
+ * fused in one pass:
+ *   d_i = s_i (1 + theta dt g_i) + sum_{j in N(i)} a_ij,   A[i][p[i]] = u_i = -a_i
+ *   b_i = s_i V_i + s_i dt g_i (E - (1 - theta) V_i)
+ * theta = 0 evaluates the membrane current at the old step as the paper's
+ * equation does; theta = 1 takes the leak at the new step.  s_i = sigma_i
+ * c_m,i / dt.  All arrays device double[n_unknowns]; V_inout holds V^k on
+ * entry and V^{k+1} on return.
+ */
+hines_status hines_cable_step(hines_plan_t plan, const double *s, const double *g, const double *u, double *V_inout,
+                              double dt, double E, int32_t theta, hines_stream_t stream);
+
+/*
+ * Solve with the passive-cable matrix of hines_cable_step (same d and u, any
+ * right-hand side), in place: rhs_inout holds y on entry and A^{-1} y on
+ * return.  The adjoint of a step is this solve, A being symmetric.
+ */
+hines_status hines_cable_solve(hines_plan_t plan, const double *s, const double *g, const double *u,
+                               double *rhs_inout, double dt, int32_t theta, hines_stream_t stream);
+
+/*
+ * Adjoint gather for x = A^{-1} b with lambda = A^{-1} xbar (A symmetric, so
+ * lambda is a second Hines solve):
+ *   grad_d[i] = -lambda_i x_i
+ *   grad_u[i] = -(lambda_i x_{p(i)} + lambda_{p(i)} x_i)   (i > 0; 0 at a cell's root)
+ * All arrays device double[n_unknowns].  No paper counterpart.
+ */
+hines_status hines_grad_du(hines_plan_t plan, const double *lambda, const double *x, double *grad_d, double *grad_u,
+                           hines_stream_t stream);
+
+/*
+ * Reverse step of a passive-cable rollout with loss
+ * L = sum_cells sum_k (V^k_root - target_cell)^2, for the step V^{k-1} -> V^k
+ * of hines_cable_step.  Given lambda = A^{-1} Vbar^k, accumulates
+ *   grad_g[i] += lambda_i s_i dt (E - (1 - theta) V^{k-1}_i) - theta s_i dt lambda_i V^k_i
+ *   grad_a[i] += -(lambda_i - lambda_{p(i)}) (V^k_i - V^k_{p(i)})     (i > 0)
+ * and writes Vbar^{k-1} = lambda s (1 - (1 - theta) dt g), plus
+ * 2 (V^{k-1}_root - target) at every cell root when add_loss_term != 0.
+ *   target  device double[n_cells]; other arrays device double[n_unknowns].
+ */
+hines_status hines_cable_adjoint_step(hines_plan_t plan, const double *lambda, const double *V_k, const double *V_km1,
+                                      const double *s, const double *g, const double *target, double dt, double E,
+                                      int32_t theta, int32_t add_loss_term, double *grad_g, double *grad_a,
+                                      double *vbar_out, hines_stream_t stream);
+
+/*
+ * Loss seed: vbar[root of c] += 2 (V[root of c] - target[c]) for every cell.
+ * Device arrays; used for the last step of a rollout.
+ */
+hines_status hines_cable_loss_seed(hines_plan_t plan, const double *V, const double *target, double *vbar,
+                                   hines_stream_t stream);
+
+/* Read (synchronously) and clear the plan's device status word. */
+hines_status hines_plan_status(hines_plan_t plan, int32_t *status_out);
+
+/* Static text of a status code. */
+const char *hines_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HINES_H */

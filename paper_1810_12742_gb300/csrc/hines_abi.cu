@@ -1,0 +1,294 @@
+// C-ABI of libhines: plan lifetime, argument checks and kernel dispatch.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/hines.h"
+#include "kernels.h"
+#include "plan.h"
+
+struct hines_plan_s {
+  hines::HostPlan host;
+  hines::DevPlan dev;
+  int device = -1;
+  bool host_only = false;
+  void* meta = nullptr;
+  void* work = nullptr;
+  int64_t meta_bytes = 0;
+  int64_t work_bytes = 0;
+};
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Copy the host plan's arrays into one device allocation and point the
+// device view at them; allocate the workspace.
+hines_status upload(hines_plan_t p, int cta_threads) {
+  const hines::HostPlan& H = p->host;
+  struct Item {
+    const void* src;
+    size_t bytes;
+    const void** dst;
+  };
+  hines::DevPlan& D = p->dev;
+  std::vector<Item> items = {
+      {H.cell_off.data(), H.cell_off.size() * 8, (const void**)&D.cell_off},
+      {H.task_cell.data(), H.task_cell.size() * 4, (const void**)&D.task_cell},
+      {H.cell_nlvl.data(), H.cell_nlvl.size() * 4, (const void**)&D.cell_nlvl},
+      {H.cell_lvl_off.data(), H.cell_lvl_off.size() * 8, (const void**)&D.cell_lvl_off},
+      {H.lvl_ptr.data(), H.lvl_ptr.size() * 4, (const void**)&D.lvl_ptr},
+      {H.order.data(), H.order.size() * 4, (const void**)&D.order},
+      {H.br_first.data(), H.br_first.size() * 8, (const void**)&D.br_first},
+      {H.br_len.data(), H.br_len.size() * 4, (const void**)&D.br_len},
+      {H.br_parent.data(), H.br_parent.size() * 4, (const void**)&D.br_parent},
+      {H.child_ptr.data(), H.child_ptr.size() * 4, (const void**)&D.child_ptr},
+      {H.child.data(), H.child.size() * 4, (const void**)&D.child},
+  };
+  size_t total = 256;  // status word first
+  for (auto& it : items) total += align256(it.bytes > 0 ? it.bytes : 1);
+  if (cudaMalloc(&p->meta, total) != cudaSuccess) {
+    cudaGetLastError();
+    p->meta = nullptr;
+    return HINES_ERR_OOM;
+  }
+  p->meta_bytes = (int64_t)total;
+  char* base = static_cast<char*>(p->meta);
+  if (cudaMemset(base, 0, 256) != cudaSuccess) return HINES_ERR_CUDA;
+  D.status = reinterpret_cast<int32_t*>(base);
+  size_t off = 256;
+  for (auto& it : items) {
+    if (it.bytes > 0 && cudaMemcpy(base + off, it.src, it.bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+      return HINES_ERR_CUDA;
+    *it.dst = base + off;
+    off += align256(it.bytes > 0 ? it.bytes : 1);
+  }
+  const size_t n = (size_t)H.n_unknowns, nb = H.br_first.size(), nc = (size_t)H.n_cells;
+  const size_t fac_b = align256(n * 8 + 8), cd_b = align256(nb * 8 + 8), red_b = align256(nc * 8 + 8);
+  const size_t wtotal = fac_b + 2 * cd_b + red_b;
+  if (cudaMalloc(&p->work, wtotal) != cudaSuccess) {
+    cudaGetLastError();
+    p->work = nullptr;
+    return HINES_ERR_OOM;
+  }
+  p->work_bytes = (int64_t)wtotal;
+  char* w = static_cast<char*>(p->work);
+  D.fac = w;
+  D.cd = w + fac_b;
+  D.cb = w + fac_b + cd_b;
+  D.red = w + fac_b + 2 * cd_b;
+  D.n_cells = H.n_cells;
+  D.n_tasks = H.n_cells;
+  D.cta_threads = cta_threads;
+  D.n_unknowns = H.n_unknowns;
+  D.n_branches = (int64_t)nb;
+  return HINES_OK;
+}
+
+hines_status check_plan(hines_plan_t p) {
+  if (!p || p->host_only) return HINES_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HINES_ERR_CUDA;
+  if (dev != p->device) return HINES_ERR_DEVICE;
+  return HINES_OK;
+}
+
+hines_status launched(cudaError_t e) { return e == cudaSuccess ? HINES_OK : HINES_ERR_CUDA; }
+
+bool need(hines_plan_t p, const void* a) { return a != nullptr || p->host.n_unknowns == 0; }
+
+}  // namespace
+
+extern "C" {
+
+hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t* ncomp, const int32_t* parent,
+                               const hines_plan_opts* opts) {
+  if (!out) return HINES_ERR_INVALID_ARG;
+  *out = nullptr;
+  hines_plan_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  for (int k = 0; k < 5; ++k)
+    if (o.reserved[k] != 0) return HINES_ERR_INVALID_ARG;
+  if (o.cta_threads == 0) o.cta_threads = 256;
+  if (o.cta_threads < 32 || o.cta_threads > 1024 || (o.cta_threads % 32) != 0) return HINES_ERR_INVALID_ARG;
+  hines_plan_t p = new (std::nothrow) hines_plan_s();
+  if (!p) return HINES_ERR_OOM;
+  int rc;
+  try {
+    rc = hines::build_host_plan(n_cells, ncomp, parent, o.split_branches, p->host);
+  } catch (const std::bad_alloc&) {
+    rc = HINES_ERR_OOM;
+  }
+  if (rc != HINES_OK) {
+    delete p;
+    return (hines_status)rc;
+  }
+  p->host_only = o.host_only != 0;
+  if (!p->host_only) {
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+      cudaGetLastError();
+      delete p;
+      return HINES_ERR_CUDA;
+    }
+    hines_status st = upload(p, o.cta_threads);
+    if (st != HINES_OK) {
+      hines_plan_destroy(p);
+      return st;
+    }
+  }
+  *out = p;
+  return HINES_OK;
+}
+
+hines_status hines_plan_destroy(hines_plan_t p) {
+  if (!p) return HINES_OK;
+  hines_status st = HINES_OK;
+  if (p->meta || p->work) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    if (cudaDeviceSynchronize() != cudaSuccess) st = HINES_ERR_CUDA;
+    if (p->meta) cudaFree(p->meta);
+    if (p->work) cudaFree(p->work);
+    if (cur != p->device && cur >= 0) cudaSetDevice(cur);
+  }
+  delete p;
+  return st;
+}
+
+hines_status hines_plan_layout(hines_plan_t p, int64_t* cell_offsets) {
+  if (!p || !cell_offsets) return HINES_ERR_INVALID_ARG;
+  std::memcpy(cell_offsets, p->host.cell_off.data(), p->host.cell_off.size() * sizeof(int64_t));
+  return HINES_OK;
+}
+
+hines_status hines_plan_info(hines_plan_t p, hines_plan_info_t* info) {
+  if (!p || !info) return HINES_ERR_INVALID_ARG;
+  info->n_cells = p->host.n_cells;
+  info->max_levels = p->host.max_levels;
+  info->n_unknowns = p->host.n_unknowns;
+  info->n_branches = (int64_t)p->host.br_first.size();
+  info->workspace_bytes = p->work_bytes;
+  info->metadata_bytes = p->meta_bytes;
+  return HINES_OK;
+}
+
+hines_status hines_plan_export(hines_plan_t p, int64_t* first, int64_t* len, int64_t* parent_branch, int64_t* level,
+                               int64_t* cell, int64_t* order) {
+  if (!p) return HINES_ERR_INVALID_ARG;
+  const hines::HostPlan& H = p->host;
+  const size_t nb = H.br_first.size();
+  for (size_t b = 0; b < nb; ++b) {
+    if (first) first[b] = H.br_first[b];
+    if (len) len[b] = H.br_len[b];
+    if (parent_branch) parent_branch[b] = H.br_parent[b];
+    if (level) level[b] = H.br_level[b];
+    if (cell) cell[b] = H.br_cell[b];
+    if (order) order[b] = H.order[b];
+  }
+  return HINES_OK;
+}
+
+hines_status hines_solve(hines_plan_t p, int32_t dtype, const void* d, const void* u, void* b_inout,
+                         hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need(p, d) || !need(p, u) || !need(p, b_inout)) return HINES_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (dtype == HINES_F64)
+    return launched(hines::launch_solve_f64(p->dev, (const double*)d, (const double*)u, (double*)b_inout, s));
+  if (dtype == HINES_F32)
+    return launched(hines::launch_solve_f32(p->dev, (const float*)d, (const float*)u, (float*)b_inout, s));
+  return HINES_ERR_INVALID_ARG;
+}
+
+hines_status hines_solve_refine(hines_plan_t p, const float* d, const float* u, const float* b, double* x_out,
+                                int32_t refine_steps, double* cell_relres, hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need(p, d) || !need(p, u) || !need(p, b) || !need(p, x_out)) return HINES_ERR_INVALID_ARG;
+  if (refine_steps < 0 || refine_steps > 4) return HINES_ERR_INVALID_ARG;
+  return launched(hines::launch_solve_refine(p->dev, d, u, b, x_out, refine_steps, cell_relres,
+                                             reinterpret_cast<cudaStream_t>(stream)));
+}
+
+hines_status hines_cable_step(hines_plan_t p, const double* s, const double* g, const double* u, double* V_inout,
+                              double dt, double E, int32_t theta, hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need(p, s) || !need(p, g) || !need(p, u) || !need(p, V_inout)) return HINES_ERR_INVALID_ARG;
+  if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
+  return launched(
+      hines::launch_cable_step(p->dev, s, g, u, V_inout, dt, E, theta, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+hines_status hines_cable_solve(hines_plan_t p, const double* s, const double* g, const double* u, double* rhs_inout,
+                               double dt, int32_t theta, hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need(p, s) || !need(p, g) || !need(p, u) || !need(p, rhs_inout)) return HINES_ERR_INVALID_ARG;
+  if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
+  return launched(
+      hines::launch_cable_solve(p->dev, s, g, u, rhs_inout, dt, theta, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+hines_status hines_grad_du(hines_plan_t p, const double* lambda, const double* x, double* grad_d, double* grad_u,
+                           hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need(p, lambda) || !need(p, x) || !need(p, grad_d) || !need(p, grad_u)) return HINES_ERR_INVALID_ARG;
+  return launched(hines::launch_grad_du(p->dev, lambda, x, grad_d, grad_u, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+hines_status hines_cable_adjoint_step(hines_plan_t p, const double* lambda, const double* V_k, const double* V_km1,
+                                      const double* s, const double* g, const double* target, double dt, double E,
+                                      int32_t theta, int32_t add_loss_term, double* grad_g, double* grad_a,
+                                      double* vbar_out, hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need(p, lambda) || !need(p, V_k) || !need(p, V_km1) || !need(p, s) || !need(p, g) || !need(p, grad_g) ||
+      !need(p, grad_a) || !need(p, vbar_out))
+    return HINES_ERR_INVALID_ARG;
+  if (add_loss_term && !target && p->host.n_cells > 0) return HINES_ERR_INVALID_ARG;
+  if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
+  return launched(hines::launch_cable_adjoint_step(p->dev, lambda, V_k, V_km1, s, g, target, dt, E, theta,
+                                                   add_loss_term, grad_g, grad_a, vbar_out,
+                                                   reinterpret_cast<cudaStream_t>(stream)));
+}
+
+hines_status hines_cable_loss_seed(hines_plan_t p, const double* V, const double* target, double* vbar,
+                                   hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need(p, V) || !need(p, vbar) || (!target && p->host.n_cells > 0)) return HINES_ERR_INVALID_ARG;
+  return launched(hines::launch_cable_loss_seed(p->dev, V, target, vbar, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+hines_status hines_plan_status(hines_plan_t p, int32_t* status_out) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!status_out) return HINES_ERR_INVALID_ARG;
+  if (cudaMemcpy(status_out, p->dev.status, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HINES_ERR_CUDA;
+  if (cudaMemset(p->dev.status, 0, sizeof(int32_t)) != cudaSuccess) return HINES_ERR_CUDA;
+  return HINES_OK;
+}
+
+const char* hines_status_string(int32_t status) {
+  switch (status) {
+    case HINES_OK: return "ok";
+    case HINES_ERR_INVALID_ARG: return "invalid argument";
+    case HINES_ERR_NOT_HINES_ORDER: return "parent array not in Hines order (need p[0] = -1, 0 <= p[i] < i)";
+    case HINES_ERR_OOM: return "out of memory";
+    case HINES_ERR_CUDA: return "CUDA runtime error";
+    case HINES_ERR_TIMEOUT: return "bounded device wait timed out";
+    case HINES_WARN_REFINE: return "iterative refinement did not contract";
+    case HINES_ERR_DEVICE: return "plan belongs to another device";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

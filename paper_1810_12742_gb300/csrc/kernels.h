@@ -1,0 +1,52 @@
+// Device-side plan view and kernel launchers (internal to libhines).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hines {
+
+// Device copy of the host plan (pointers into one metadata allocation) and
+// the plan's workspace.
+struct DevPlan {
+  int32_t n_cells = 0;
+  int32_t n_tasks = 0;
+  int32_t cta_threads = 256;
+  int64_t n_unknowns = 0;
+  int64_t n_branches = 0;
+  const int64_t* cell_off = nullptr;      // [n_cells + 1]
+  const int32_t* task_cell = nullptr;     // [n_tasks]
+  const int32_t* cell_nlvl = nullptr;     // [n_cells]
+  const int64_t* cell_lvl_off = nullptr;  // [n_cells]
+  const int32_t* lvl_ptr = nullptr;       // per cell nlvl + 1
+  const int32_t* order = nullptr;         // [nb]
+  const int64_t* br_first = nullptr;      // [nb]
+  const int32_t* br_len = nullptr;        // [nb]
+  const int32_t* br_parent = nullptr;     // [nb]
+  const int32_t* child_ptr = nullptr;     // [nb + 1]
+  const int32_t* child = nullptr;         // [nb - n_roots]
+  // workspace
+  void* fac = nullptr;    // n_unknowns * 8 bytes: eliminated diagonal (FP64), or two FP32 arrays
+  void* cd = nullptr;     // n_branches * 8 bytes: child-to-parent diagonal contribution
+  void* cb = nullptr;     // n_branches * 8 bytes: child-to-parent right-hand-side contribution
+  void* red = nullptr;    // n_cells * 8 bytes: per-cell reductions
+  int32_t* status = nullptr;  // device status word
+};
+
+cudaError_t launch_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s);
+cudaError_t launch_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s);
+cudaError_t launch_solve_refine(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
+                                int steps, double* relres, cudaStream_t s);
+cudaError_t launch_cable_step(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
+                              double dt, double E, int theta, cudaStream_t s);
+cudaError_t launch_cable_solve(const DevPlan& P, const double* sv, const double* g, const double* u, double* y,
+                               double dt, int theta, cudaStream_t s);
+cudaError_t launch_grad_du(const DevPlan& P, const double* lam, const double* x, double* gd, double* gu,
+                           cudaStream_t s);
+cudaError_t launch_cable_adjoint_step(const DevPlan& P, const double* lam, const double* Vk, const double* Vkm1,
+                                      const double* sv, const double* g, const double* target, double dt, double E,
+                                      int theta, int add_loss, double* grad_g, double* grad_a, double* vbar,
+                                      cudaStream_t s);
+cudaError_t launch_cable_loss_seed(const DevPlan& P, const double* V, const double* target, double* vbar,
+                                   cudaStream_t s);
+
+}  // namespace hines

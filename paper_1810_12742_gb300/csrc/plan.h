@@ -1,0 +1,35 @@
+// Host-side plan of the batched Hines solver (internal to libhines).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace hines {
+
+// Branch decomposition and schedule of a batch of cells.  Branch ids are
+// global: the branches of cell c are [cell_br_off[c], cell_br_off[c+1]),
+// numbered by their first compartment.
+struct HostPlan {
+  int32_t n_cells = 0;
+  int64_t n_unknowns = 0;
+  int32_t max_levels = 0;
+  std::vector<int64_t> cell_off;     // [n_cells + 1] natural-layout offsets
+  std::vector<int64_t> cell_br_off;  // [n_cells + 1]
+  std::vector<int64_t> br_first;     // natural-layout index of the proximal compartment
+  std::vector<int32_t> br_len;       // compartments
+  std::vector<int32_t> br_parent;    // global parent branch id, -1 for a root branch
+  std::vector<int32_t> br_level;     // ancestor branches
+  std::vector<int32_t> br_cell;      // owning cell
+  std::vector<int32_t> child_ptr;    // [nb + 1] CSR of children per branch
+  std::vector<int32_t> child;        // children, by first compartment descending
+  std::vector<int32_t> order;        // per cell, level 0..L-1, length desc then id
+  std::vector<int32_t> cell_nlvl;    // [n_cells]
+  std::vector<int64_t> cell_lvl_off; // [n_cells] index of the cell's first entry in lvl_ptr
+  std::vector<int32_t> lvl_ptr;      // per cell nlvl + 1 indices into order
+  std::vector<int32_t> task_cell;    // cells in processing order (cost descending)
+};
+
+// Return codes follow hines_status.
+int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,
+                    HostPlan& out);
+
+}  // namespace hines

@@ -1,0 +1,253 @@
+"""Thin ctypes binding of libhines (argument marshalling only).
+
+Every compute step runs in the library's CUDA kernels; PyTorch only provides
+device memory and the current stream.  The names follow include/hines.h.
+There is no CPU fallback: loading fails loudly when libhines.so is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libhines.so")
+_lock = threading.Lock()
+_lib = None
+
+HINES_OK = 0
+HINES_ERR_INVALID_ARG = 1
+HINES_ERR_NOT_HINES_ORDER = 2
+HINES_ERR_OOM = 3
+HINES_ERR_CUDA = 4
+HINES_ERR_TIMEOUT = 5
+HINES_WARN_REFINE = 6
+HINES_ERR_DEVICE = 7
+HINES_F64 = 0
+HINES_F32 = 1
+
+EXPORTS = [
+    "hines_plan_create", "hines_plan_destroy", "hines_plan_layout", "hines_plan_info", "hines_plan_export",
+    "hines_solve", "hines_solve_refine", "hines_cable_step", "hines_cable_solve", "hines_grad_du",
+    "hines_cable_adjoint_step", "hines_cable_loss_seed", "hines_plan_status", "hines_status_string",
+]
+
+
+class HinesError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (status {code})")
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("host_only", ctypes.c_int32), ("split_branches", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("n_unknowns", ctypes.c_int64),
+                ("n_branches", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("metadata_bytes", ctypes.c_int64)]
+
+
+def lib():
+    """Load libhines.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise ImportError(f"libhines.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+            L = ctypes.CDLL(_LIB_PATH)
+            vp, i32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+            L.hines_plan_create.argtypes = [ctypes.POINTER(vp), i32, vp, vp, ctypes.POINTER(PlanOpts)]
+            L.hines_plan_destroy.argtypes = [vp]
+            L.hines_plan_layout.argtypes = [vp, vp]
+            L.hines_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+            L.hines_plan_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+            L.hines_solve.argtypes = [vp, i32, vp, vp, vp, vp]
+            L.hines_solve_refine.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
+            L.hines_cable_step.argtypes = [vp, vp, vp, vp, vp, f64, f64, i32, vp]
+            L.hines_cable_solve.argtypes = [vp, vp, vp, vp, vp, f64, i32, vp]
+            L.hines_grad_du.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.hines_cable_adjoint_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, f64, f64, i32, i32, vp, vp, vp, vp]
+            L.hines_cable_loss_seed.argtypes = [vp, vp, vp, vp, vp]
+            L.hines_plan_status.argtypes = [vp, ctypes.POINTER(i32)]
+            L.hines_status_string.argtypes = [i32]
+            L.hines_status_string.restype = ctypes.c_char_p
+            for name in EXPORTS:
+                if name != "hines_status_string":
+                    getattr(L, name).restype = i32
+            _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().hines_status_string(int(code)).decode()
+
+
+def _check(code, where):
+    if code != HINES_OK:
+        raise HinesError(code, where)
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Plan:
+    """Branch decomposition and schedule of a batch of cells (hines_plan_create).
+
+    ncomp: compartments per cell; parent: the cells' parent arrays (cell-local,
+    p[0] = -1, p[i] < i), concatenated.  host_only builds the schedule without
+    touching the GPU (for inspection)."""
+
+    def __init__(self, ncomp, parent, split_branches: bool = False, host_only: bool = False, cta_threads: int = 0):
+        self._h = ctypes.c_void_p()
+        nc = np.ascontiguousarray(ncomp, np.int32)
+        pa = np.ascontiguousarray(parent, np.int32)
+        opts = PlanOpts(int(host_only), int(split_branches), int(cta_threads))
+        _check(lib().hines_plan_create(ctypes.byref(self._h), nc.size, _np_ptr(nc), _np_ptr(pa), ctypes.byref(opts)),
+               "hines_plan_create")
+        info = PlanInfo()
+        _check(lib().hines_plan_info(self._h, ctypes.byref(info)), "hines_plan_info")
+        self.n_cells = info.n_cells
+        self.n_unknowns = info.n_unknowns
+        self.n_branches = info.n_branches
+        self.max_levels = info.max_levels
+        self.workspace_bytes = info.workspace_bytes
+        self.metadata_bytes = info.metadata_bytes
+        self.host_only = host_only
+        off = np.empty(self.n_cells + 1, np.int64)
+        _check(lib().hines_plan_layout(self._h, _np_ptr(off)), "hines_plan_layout")
+        self.offsets = off
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self) -> dict:
+        nb = self.n_branches
+        out = {k: np.empty(nb, np.int64) for k in ("first", "len", "parent_branch", "level", "cell", "order")}
+        _check(lib().hines_plan_export(self._h, *(_np_ptr(out[k]) for k in
+                                                  ("first", "len", "parent_branch", "level", "cell", "order"))),
+               "hines_plan_export")
+        return out
+
+    def status(self) -> int:
+        st = ctypes.c_int32(0)
+        _check(lib().hines_plan_status(self._h, ctypes.byref(st)), "hines_plan_status")
+        return st.value
+
+    def close(self):
+        if self._h:
+            lib().hines_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------
+# torch-facing calls (device tensors, current stream)
+# ----------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def _dptr(t, dtype, n, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name}: expected contiguous {dtype} with {n} elements, got {t.dtype} {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def solve(plan: Plan, d, u, b):
+    """In place: b <- A^{-1} b for every cell (FP64 or FP32 by the tensors' dtype)."""
+    torch = _torch()
+    n = plan.n_unknowns
+    if b.dtype == torch.float64:
+        dt, code = torch.float64, HINES_F64
+    elif b.dtype == torch.float32:
+        dt, code = torch.float32, HINES_F32
+    else:
+        raise ValueError("b must be float64 or float32")
+    _check(lib().hines_solve(plan.handle, code, _dptr(d, dt, n, "d"), _dptr(u, dt, n, "u"), _dptr(b, dt, n, "b"),
+                             _stream()), "hines_solve")
+    return b
+
+
+def solve_refine(plan: Plan, d, u, b, x=None, steps: int = 2, relres=None):
+    """FP32 elimination + FP64 residual/correction refinement; returns x (float64)."""
+    torch = _torch()
+    n = plan.n_unknowns
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=b.device)
+    rr = ctypes.c_void_p(0) if relres is None else _dptr(relres, torch.float64, plan.n_cells, "relres")
+    _check(lib().hines_solve_refine(plan.handle, _dptr(d, torch.float32, n, "d"), _dptr(u, torch.float32, n, "u"),
+                                    _dptr(b, torch.float32, n, "b"), _dptr(x, torch.float64, n, "x"), int(steps), rr,
+                                    _stream()), "hines_solve_refine")
+    return x
+
+
+def cable_step(plan: Plan, s, g, u, V, dt: float, E: float, theta: int = 1):
+    """One fused rebuild + solve step of the passive cable; V advanced in place."""
+    torch = _torch()
+    n = plan.n_unknowns
+    f = torch.float64
+    _check(lib().hines_cable_step(plan.handle, _dptr(s, f, n, "s"), _dptr(g, f, n, "g"), _dptr(u, f, n, "u"),
+                                  _dptr(V, f, n, "V"), float(dt), float(E), int(theta), _stream()),
+           "hines_cable_step")
+    return V
+
+
+def cable_solve(plan: Plan, s, g, u, y, dt: float, theta: int = 1):
+    torch = _torch()
+    n = plan.n_unknowns
+    f = torch.float64
+    _check(lib().hines_cable_solve(plan.handle, _dptr(s, f, n, "s"), _dptr(g, f, n, "g"), _dptr(u, f, n, "u"),
+                                   _dptr(y, f, n, "y"), float(dt), int(theta), _stream()), "hines_cable_solve")
+    return y
+
+
+def grad_du(plan: Plan, lam, x, grad_d=None, grad_u=None):
+    torch = _torch()
+    n = plan.n_unknowns
+    f = torch.float64
+    grad_d = torch.empty_like(x) if grad_d is None else grad_d
+    grad_u = torch.empty_like(x) if grad_u is None else grad_u
+    _check(lib().hines_grad_du(plan.handle, _dptr(lam, f, n, "lambda"), _dptr(x, f, n, "x"),
+                               _dptr(grad_d, f, n, "grad_d"), _dptr(grad_u, f, n, "grad_u"), _stream()),
+           "hines_grad_du")
+    return grad_d, grad_u
+
+
+def cable_adjoint_step(plan: Plan, lam, V_k, V_km1, s, g, target, dt, E, theta, add_loss_term, grad_g, grad_a, vbar):
+    torch = _torch()
+    n = plan.n_unknowns
+    f = torch.float64
+    tg = _dptr(target, f, plan.n_cells, "target")
+    _check(lib().hines_cable_adjoint_step(plan.handle, _dptr(lam, f, n, "lambda"), _dptr(V_k, f, n, "V_k"),
+                                          _dptr(V_km1, f, n, "V_km1"), _dptr(s, f, n, "s"), _dptr(g, f, n, "g"), tg,
+                                          float(dt), float(E), int(theta), int(add_loss_term),
+                                          _dptr(grad_g, f, n, "grad_g"), _dptr(grad_a, f, n, "grad_a"),
+                                          _dptr(vbar, f, n, "vbar"), _stream()), "hines_cable_adjoint_step")
+
+
+def cable_loss_seed(plan: Plan, V, target, vbar):
+    torch = _torch()
+    n = plan.n_unknowns
+    f = torch.float64
+    _check(lib().hines_cable_loss_seed(plan.handle, _dptr(V, f, n, "V"), _dptr(target, f, plan.n_cells, "target"),
+                                       _dptr(vbar, f, n, "vbar"), _stream()), "hines_cable_loss_seed")

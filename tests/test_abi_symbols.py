@@ -1,0 +1,57 @@
+"""The C-ABI library loads without a GPU and exports every entry point that
+include/hines.h declares; argument errors come back as status codes."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+
+from paper_1810_12742_gb300 import hines as H
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "hines.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hines_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_symbols() == sorted(H.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = H.lib()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", H._LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (hines_\w+)", out))
+    assert set(declared_symbols()) <= exported
+
+
+def test_status_strings():
+    for code in range(8):
+        assert H.status_string(code) not in ("", "unknown status")
+    assert H.status_string(99) == "unknown status"
+
+
+def test_argument_errors_without_gpu():
+    L = H.lib()
+    h = ctypes.c_void_p()
+    nc = np.array([2], np.int32)
+    pa = np.array([-1, 0], np.int32)
+    assert L.hines_plan_create(None, 1, nc.ctypes.data_as(ctypes.c_void_p), pa.ctypes.data_as(ctypes.c_void_p),
+                               None) == H.HINES_ERR_INVALID_ARG
+    opts = H.PlanOpts(1, 0, 0)
+    opts.reserved[2] = 1
+    assert L.hines_plan_create(ctypes.byref(h), 1, nc.ctypes.data_as(ctypes.c_void_p),
+                               pa.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts)) == H.HINES_ERR_INVALID_ARG
+    opts = H.PlanOpts(1, 0, 48)  # not a multiple of 32
+    assert L.hines_plan_create(ctypes.byref(h), 1, nc.ctypes.data_as(ctypes.c_void_p),
+                               pa.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts)) == H.HINES_ERR_INVALID_ARG
+    plan = H.Plan(nc, pa, host_only=True)
+    # a host-only plan refuses device work before touching CUDA
+    assert L.hines_solve(plan.handle, H.HINES_F64, None, None, None, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_plan_destroy(None) == H.HINES_OK

@@ -1,0 +1,190 @@
+"""Host planner: an independent Python statement of the decomposition,
+splitting and ordering rules must agree bit for bit with the C++ planner
+(host-only plans, no GPU needed)."""
+import numpy as np
+import pytest
+
+from paper_1810_12742_gb300 import hines as H
+from paper_1810_12742_gb300 import inputs as I
+from tests.helpers import tree_zoo
+
+
+def py_branches(p):
+    """Branches of one cell: maximal runs i, i+1, ... where each next
+    compartment's parent is its predecessor and that predecessor has one child."""
+    n = len(p)
+    nchild = np.bincount(np.asarray(p[1:], np.int64), minlength=n) if n > 1 else np.zeros(n, np.int64)
+    br = []  # [first, len, parent_branch, level]
+    owner = np.empty(n, np.int64)
+    for i in range(n):
+        if i == 0 or p[i] != i - 1 or nchild[p[i]] >= 2:
+            pb = -1 if i == 0 else int(owner[p[i]])
+            br.append([i, 1, pb, 0 if pb < 0 else br[pb][3] + 1])
+        else:
+            br[-1][1] += 1
+        owner[i] = len(br) - 1
+    return br
+
+
+def py_split(cells):
+    """Section 6 splitting: per level over the whole batch, cut branches longer
+    than the level mean (strictly) after ceil(len/2) compartments."""
+    level = 0
+    while True:
+        lens = [b[1] for bs in cells for b in bs if b[3] == level]
+        if not lens:
+            return cells
+        mean = float(np.sum(np.array(lens, np.float64))) / len(lens)
+        new_cells = []
+        for bs in cells:
+            out, prox, dist = [], {}, {}
+            for j, b in enumerate(bs):
+                prox[j] = len(out)
+                if b[3] == level and b[1] > mean and b[1] >= 2:
+                    k = (b[1] + 1) // 2
+                    out.append([b[0], k, b[2], b[3]])
+                    dist[j] = len(out)
+                    out.append([b[0] + k, b[1] - k, ("prox", j), b[3] + 1])
+                else:
+                    dist[j] = prox[j]
+                    out.append(list(b))
+            for b in out:
+                if isinstance(b[2], tuple):
+                    b[2] = prox[b[2][1]]
+                elif b[2] >= 0:
+                    b[2] = dist[b[2]]
+            for b in out:
+                b[3] = 0 if b[2] < 0 else out[b[2]][3] + 1
+            new_cells.append(out)
+        cells = new_cells
+        level += 1
+
+
+def py_plan(ncomp, parent, split=False):
+    off = np.concatenate(([0], np.cumsum(ncomp))).astype(np.int64)
+    cells = [py_branches(parent[off[c]:off[c + 1]]) for c in range(len(ncomp))]
+    if split:
+        cells = py_split(cells)
+    first, length, pbr, level, cell, order = [], [], [], [], [], []
+    base = 0
+    for c, bs in enumerate(cells):
+        for b in bs:
+            first.append(off[c] + b[0])
+            length.append(b[1])
+            pbr.append(-1 if b[2] < 0 else base + b[2])
+            level.append(b[3])
+            cell.append(c)
+        ids = list(range(base, base + len(bs)))
+        ids.sort(key=lambda g: (level[g], -length[g], g))
+        order += ids
+        base += len(bs)
+    return {k: np.array(v, np.int64) for k, v in
+            dict(first=first, len=length, parent_branch=pbr, level=level, cell=cell, order=order).items()}
+
+
+def _compare(ncomp, parent, split):
+    plan = H.Plan(ncomp, parent, split_branches=split, host_only=True)
+    got = plan.export()
+    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split)
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+    assert plan.n_unknowns == int(np.sum(ncomp))
+    return got
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_zoo_matches_restatement(split):
+    rng = np.random.default_rng(21)
+    trees = []
+    for n in (1, 2, 5, 33, 250):
+        trees += list(tree_zoo(rng, n).values())
+    ncomp = [t.size for t in trees]
+    _compare(ncomp, np.concatenate(trees), split)
+
+
+@pytest.mark.parametrize("name", ["fp64_small", "fp64_uniform", "uneven_steps", "adjoint"])
+@pytest.mark.parametrize("split", [False, True])
+def test_workload_samples_match_restatement(name, split):
+    w = I.WORKLOADS[name]
+    cells = np.arange(min(w.n_cells, 24))
+    if name == "uneven_steps":  # make sure large cells are included
+        cls = I.cell_classes(w)
+        cells = np.concatenate([np.nonzero(cls == 0)[0][:8], np.nonzero(cls == 1)[0][:3]])
+    ncomp, parent = I.population_trees(w, cells)
+    got = _compare(ncomp, parent, split)
+    # structure: children come after parents, every cell has one root branch
+    pb = got["parent_branch"]
+    assert (pb < np.arange(pb.size)).all()
+    assert ((pb < 0).sum()) == len(cells)
+
+
+def test_branches_cover_compartments_and_backward_order_is_valid():
+    rng = np.random.default_rng(22)
+    trees = [I.random_chainy_tree(rng, int(m)) for m in rng.integers(1, 400, 30)]
+    ncomp = np.array([t.size for t in trees])
+    parent = np.concatenate(trees)
+    for split in (False, True):
+        e = H.Plan(ncomp, parent, split_branches=split, host_only=True).export()
+        # every compartment in exactly one branch, branches are parent chains
+        cover = np.zeros(parent.size, int)
+        off = np.concatenate(([0], np.cumsum(ncomp)))
+        for f, l, c in zip(e["first"], e["len"], e["cell"]):
+            cover[f:f + l] += 1
+            loc = np.arange(f, f + l) - off[c]
+            assert (parent[f + 1:f + l] == loc[:-1]).all()
+        assert (cover == 1).all()
+        # the proximal compartment's parent is the last compartment of the parent branch
+        for b in range(e["first"].size):
+            pbid = e["parent_branch"][b]
+            if pbid >= 0:
+                assert parent[e["first"][b]] + off[e["cell"][b]] == e["first"][pbid] + e["len"][pbid] - 1
+        # reversed processing order (deepest level first) visits children before parents
+        pos = np.empty_like(e["order"])
+        pos[e["order"]] = np.arange(pos.size)
+        has = e["parent_branch"] >= 0
+        assert (pos[e["parent_branch"][has]] < pos[np.nonzero(has)[0]]).all()
+
+
+def test_split_shortens_long_branches():
+    rng = np.random.default_rng(23)
+    w = I.WORKLOADS["fp64_uniform"]
+    ncomp, parent = I.population_trees(w, np.arange(8))
+    a = H.Plan(ncomp, parent, split_branches=False, host_only=True)
+    b = H.Plan(ncomp, parent, split_branches=True, host_only=True)
+    ea, eb = a.export(), b.export()
+    assert b.n_branches > a.n_branches
+    assert eb["len"].max() <= ea["len"].max()
+    assert b.max_levels > a.max_levels
+
+
+def test_planner_time_is_linear():
+    """Section 6: the setup work is linear in the number of cells."""
+    import time
+    w = I.WORKLOADS["fp64_uniform"]
+    ncomp, parent = I.population_trees(w, np.arange(64))
+    t = []
+    for rep in (1, 8):
+        nc = np.tile(ncomp, rep)
+        pa = np.tile(parent, rep)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            H.Plan(nc, pa, split_branches=True, host_only=True)
+        t.append((time.perf_counter() - t0) / 3)
+    assert t[1] < 8 * t[0] * 2.5  # linear within noise
+
+
+def test_invalid_inputs():
+    with pytest.raises(H.HinesError) as e:
+        H.Plan([3], np.array([-1, 0, 2], np.int32), host_only=True)
+    assert e.value.code == H.HINES_ERR_NOT_HINES_ORDER
+    with pytest.raises(H.HinesError) as e:
+        H.Plan([2], np.array([0, 0], np.int32), host_only=True)
+    assert e.value.code == H.HINES_ERR_NOT_HINES_ORDER
+    with pytest.raises(H.HinesError) as e:
+        H.Plan([-1], np.array([], np.int32), host_only=True)
+    assert e.value.code == H.HINES_ERR_INVALID_ARG
+    # empty batch and empty cells are fine
+    p = H.Plan([], np.array([], np.int32), host_only=True)
+    assert p.n_cells == 0 and p.n_branches == 0
+    p = H.Plan([0, 3, 0], np.array([-1, 0, 1], np.int32), host_only=True)
+    assert p.n_branches == 1 and list(p.offsets) == [0, 0, 3, 3]
