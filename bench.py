@@ -1,0 +1,293 @@
+"""Benchmark of the batched Hines solver on one GB300 (one JSON line).
+
+Step = one mixed-precision solve of the whole uneven population (8192 cells,
+70% small / 30% large, about 228M compartments): FP32 elimination with FP64
+residual refinement (hines_solve_refine), inputs resident in HBM.  The same
+batch is also solved in plain FP64 (hines_solve) for the FP32+refine vs FP64
+comparison.  The inputs (4.6 GB) are larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank solves its own replica of the population
+(weak scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic bytes per compartment (compulsory traffic of one solve):
+#   FP32 + refine: read d, u, b in FP32 (12 B) + write x in FP64 (8 B)
+#   FP64:          read d, u, b in FP64 (24 B) + write x in FP64 (8 B)
+BYTES_REFINE = 20
+BYTES_F64 = 32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uneven_mixed")
+    ap.add_argument("--margin", type=float, default=0.1)
+    ap.add_argument("--refine-steps", type=int, default=2)
+    ap.add_argument("--cells", type=int, default=0, help="use only the first N cells (small cases, profiling)")
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_record(kernel):
+    """ncu DRAM bytes per compartment for `kernel`, if captured on the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        from paper_1810_12742_gb300 import _build
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+        if rec and rec.get("source_digest") == _build._digest():
+            return float(rec["dram_bytes_per_unknown"])
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(pop, widen, budget_s=8.0):
+    """The oracle as it stands, on the host cores: repeated full-batch solves
+    until about budget_s seconds of wall time."""
+    import oracle
+    nthreads = os.cpu_count() or 1
+    d, u, b = ((pop[k].astype(np.float32).astype(np.float64) if widen else pop[k]) for k in ("d", "u", "b"))
+    oracle.solve_batch(pop["ncomp"][:4], pop["parent"][:int(pop["offsets"][4])], d, u, b, nthreads)  # load
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.solve_batch(pop["ncomp"], pop["parent"], d, u, b, nthreads)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 50:
+            break
+    n = int(pop["offsets"][-1])
+    return {"value": n * reps / el, "unit": "compartments/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"{reps} x the full batch ({n} compartments), serial FP64 Hines solve per cell, "
+                      f"OpenMP over cells"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_1810_12742_gb300 import inputs as I
+    w = I.WORKLOADS[args.workload]
+    cells = np.arange(args.cells) if args.cells else None
+    pop = I.population(w, cells=cells, margin=args.margin)
+    n = int(pop["offsets"][-1])
+    widen = True
+    config = {"workload": w.name, "cells": int(pop["ncomp"].size), "compartments": n,
+              "leak_margin": args.margin, "refine_steps": args.refine_steps,
+              "l2": "inputs (4.6 GB at full size) exceed L2; no flush",
+              "seed": f"numpy PCG64 per cell, base {I.SEED_BASE}"}
+    metric = "compartments solved/sec per GB300 and % of HBM roofline, FP32+refine vs FP64"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = cpu_baseline(pop, widen)
+        line = {"impl": "reference", "metric": metric, "value": cb["value"], "unit": "compartments/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": n / cb["value"] * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config, "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "compartments/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1810_12742_gb300 import hines as H
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    plan = H.Plan(pop["ncomp"], pop["parent"])
+    f32 = {k: torch.as_tensor(pop[k].astype(np.float32)).cuda() for k in ("d", "u", "b")}
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        H.solve_refine(plan, f32["d"], f32["u"], f32["b"], x, args.refine_steps)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    ms_step = ms_total / args.steps
+    value = n * args.steps * world / (ms_total * 1e-3)
+    status = plan.status()
+
+    # parity on a sample of cells against the oracle (FP64 solve of the FP32 inputs widened exactly)
+    import oracle
+    rng = np.random.default_rng(1)
+    sample = np.sort(rng.choice(pop["ncomp"].size, min(64, pop["ncomp"].size), replace=False))
+    xs = x.cpu().numpy()
+    off = pop["offsets"]
+    err = 0.0
+    for c in sample:
+        sl = slice(off[c], off[c + 1])
+        if off[c + 1] == off[c]:
+            continue
+        ref = oracle.solve_batch(pop["ncomp"][c:c + 1], pop["parent"][sl],
+                                 *(pop[k][sl].astype(np.float32).astype(np.float64) for k in ("d", "u", "b")))
+        err = max(err, float(np.abs(xs[sl] - ref).max() / np.abs(ref).max()))
+
+    # FP64 solve of the same batch (per-solve events around the kernel only)
+    f64 = {k: torch.as_tensor(pop[k]).cuda() for k in ("d", "u", "b")}
+    x64 = torch.empty_like(f64["b"])
+    ms64 = []
+    for it in range(args.warmup + args.fp64_steps):
+        x64.copy_(f64["b"])
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        H.solve(plan, f64["d"], f64["u"], x64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            ms64.append(a0.elapsed_time(a1))
+    ms64 = max_over_ranks(float(np.mean(ms64)))
+    del f64, x64
+
+    # end to end through the public API with pinned host buffers
+    host = {k: torch.as_tensor(pop[k].astype(np.float32)).pin_memory() for k in ("d", "u", "b")}
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for it in range(1 + args.e2e_steps):
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        H.solve_refine_host(plan, host["d"], host["u"], host["b"], xh, args.refine_steps)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 1:
+            e2e_ms.append(a0.elapsed_time(a1))
+    e2e_ms = max_over_ranks(float(np.mean(e2e_ms)))
+
+    peak, peak_kind = load_peaks()
+    achieved = BYTES_REFINE * n / (ms_step * 1e-3) / 1e9
+    tr = traffic_record("k_solve_refine")
+    line = {
+        "metric": metric, "value": value, "unit": "compartments/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config,
+        "max_rel_err": err, "status": status,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None if tr is None else tr * n,
+                     "kernel": "k_solve_refine", "algorithmic_bytes_per_compartment": BYTES_REFINE,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"},
+        "fp64": {"value": n / (ms64 * 1e-3), "unit": "compartments/s", "ms_per_solve": ms64,
+                 "roofline_frac": BYTES_F64 * n / (ms64 * 1e-3) / 1e9 / peak,
+                 "speedup_of_fp32_refine": ms64 / ms_step},
+        "e2e": {"value": n / (e2e_ms * 1e-3), "unit": "compartments/s",
+                "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 8 * n},
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pop, widen)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

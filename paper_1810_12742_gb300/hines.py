@@ -251,3 +251,21 @@ def cable_loss_seed(plan: Plan, V, target, vbar):
     f = torch.float64
     _check(lib().hines_cable_loss_seed(plan.handle, _dptr(V, f, n, "V"), _dptr(target, f, plan.n_cells, "target"),
                                        _dptr(vbar, f, n, "vbar"), _stream()), "hines_cable_loss_seed")
+
+
+def solve_refine_host(plan: Plan, d, u, b, x, steps: int = 2):
+    """solve_refine on host tensors (pinned for asynchronous copies): copies d,
+    u, b to device staging buffers owned by the plan object, solves, and copies
+    x back, all on the current stream."""
+    torch = _torch()
+    n = plan.n_unknowns
+    st = getattr(plan, "_staging", None)
+    if st is None:
+        st = tuple(torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)) + (
+            torch.empty(n, dtype=torch.float64, device="cuda"),)
+        plan._staging = st
+    for dst, src in zip(st[:3], (d, u, b)):
+        dst.copy_(src, non_blocking=True)
+    solve_refine(plan, st[0], st[1], st[2], st[3], steps)
+    x.copy_(st[3], non_blocking=True)
+    return x
