@@ -74,6 +74,8 @@ typedef struct {
 typedef struct {
   int32_t n_cells;
   int32_t max_levels;       /* deepest branch dependency tree (levels of Section 3) */
+  int32_t n_tasks;          /* warp tasks: groups of cells solved together by one warp */
+  int32_t reserved;
   int64_t n_unknowns;       /* total compartments */
   int64_t n_branches;       /* unbranched runs after optional splitting */
   int64_t workspace_bytes;  /* device workspace owned by the plan */
@@ -90,11 +92,15 @@ typedef struct {
  * Validates every cell (HINES_ERR_NOT_HINES_ORDER names no cell; use a
  * per-cell check on the host to find it), decomposes each tree into branches
  * (maximal unbranched runs: compartment i starts a branch when i = 0,
- * p[i] != i-1, or p[i] has two or more children), assigns levels (number of
+ * p[i] != i-1, or p[i] has two or more children), optionally splits branches
+ * longer than their level's mean (Section 6), cuts every branch longer than
+ * 32 compartments into near-equal chained pieces, assigns levels (number of
  * ancestor branches), orders the branches of every level by length
- * (descending, ties by branch index; Section 4, Fig. 4.1), and uploads the
- * metadata and a workspace to the current device.  On success *out receives
- * the plan; on failure *out is NULL.
+ * (descending, ties by branch index; Section 4, Fig. 4.1), packs cells into
+ * warp tasks (Section 4's greedy rule with the 32 lanes of a warp: cells are
+ * added, largest first, while every level of the task holds at most 32
+ * branches), and uploads the metadata and a workspace to the current device.
+ * On success *out receives the plan; on failure *out is NULL.
  */
 hines_status hines_plan_create(hines_plan_t *out, int32_t n_cells, const int32_t *ncomp, const int32_t *parent,
                                const hines_plan_opts *opts);
@@ -123,6 +129,15 @@ hines_status hines_plan_export(hines_plan_t plan, int64_t *first, int64_t *len, 
                                int64_t *level, int64_t *cell, int64_t *order);
 
 /*
+ * Copy the warp-task schedule to host arrays (NULL skips an array):
+ *   cell_task[n_cells]  task of each cell (-1 for a cell without compartments)
+ *   task_order[nb]      branches in processing order: task by task (largest
+ *        task first), level by level from 0, within a level by length
+ *        descending, then cell, then branch index
+ */
+hines_status hines_plan_export_tasks(hines_plan_t plan, int64_t *cell_task, int64_t *task_order);
+
+/*
  * Solve A x = b for every cell (Section 2, Listing 2), in place.
  *   dtype   HINES_F64 (arithmetic in FP64) or HINES_F32 (arithmetic in FP32)
  *   d       device [n_unknowns] diagonal, not modified
@@ -132,6 +147,20 @@ hines_status hines_plan_export(hines_plan_t plan, int64_t *first, int64_t *len, 
  */
 hines_status hines_solve(hines_plan_t plan, int32_t dtype, const void *d, const void *u, void *b_inout,
                          hines_stream_t stream);
+
+/*
+ * Compensated mixed-precision solve: FP32 inputs, FP64 solution, and the
+ * elimination and substitution of Listing 2 carried out in double-float
+ * arithmetic (each quantity an unevaluated sum of two FP32 numbers, products
+ * and sums made exact by error-free transformations), so that no FP64
+ * instruction is needed.  Accuracy is that of a solve in about 48-bit
+ * precision: relative error about cond(A) * 2^-50.  No paper counterpart.
+ *   d, u, b   device float[n_unknowns], not modified
+ *   x_out     device double[n_unknowns], the solution
+ * Stream-ordered; uses the plan's workspace.
+ */
+hines_status hines_solve_compensated(hines_plan_t plan, const float *d, const float *u, const float *b,
+                                     double *x_out, hines_stream_t stream);
 
 /*
  * Mixed-precision solve: elimination in FP32 on FP32 inputs, then

@@ -34,7 +34,25 @@ hines_status upload(hines_plan_t p, int cta_threads) {
     const void** dst;
   };
   hines::DevPlan& D = p->dev;
+  // per-branch metadata in warp-task order
+  std::vector<hines::BrMetaT> tmeta(H.torder.size());
+  for (size_t k = 0; k < H.torder.size(); ++k) {
+    const int32_t b = H.torder[k];
+    hines::BrMetaT& m = tmeta[k];
+    m.first = H.br_first[(size_t)b];
+    m.len = H.br_len[(size_t)b];
+    const int32_t pb = H.br_parent[(size_t)b];
+    m.pcomp = pb < 0 ? -1 : H.br_first[(size_t)pb] + H.br_len[(size_t)pb] - 1;
+    m.ppos = pb < 0 ? -1 : H.tpos[(size_t)pb];
+    m.cbeg = H.tchild_ptr[k];
+    m.cend = H.tchild_ptr[k + 1];
+  }
   std::vector<Item> items = {
+      {tmeta.data(), tmeta.size() * sizeof(hines::BrMetaT), (const void**)&D.tmeta},
+      {H.task_nlvl.data(), H.task_nlvl.size() * 4, (const void**)&D.task_nlvl},
+      {H.task_lvl_off.data(), H.task_lvl_off.size() * 8, (const void**)&D.task_lvl_off},
+      {H.tlvl_ptr.data(), H.tlvl_ptr.size() * 4, (const void**)&D.tlvl_ptr},
+      {H.tchild.data(), H.tchild.size() * 4, (const void**)&D.tchild},
       {H.cell_off.data(), H.cell_off.size() * 8, (const void**)&D.cell_off},
       {H.task_cell.data(), H.task_cell.size() * 4, (const void**)&D.task_cell},
       {H.cell_nlvl.data(), H.cell_nlvl.size() * 4, (const void**)&D.cell_nlvl},
@@ -66,8 +84,9 @@ hines_status upload(hines_plan_t p, int cta_threads) {
     off += align256(it.bytes > 0 ? it.bytes : 1);
   }
   const size_t n = (size_t)H.n_unknowns, nb = H.br_first.size(), nc = (size_t)H.n_cells;
-  const size_t fac_b = align256(n * 8 + 8), cd_b = align256(nb * 8 + 8), red_b = align256(nc * 8 + 8);
-  const size_t wtotal = fac_b + 2 * cd_b + red_b;
+  const size_t fac_b = align256(n * 8 + 8), cd_b = align256(nb * 16 + 16), cb_b = align256(nb * 8 + 8),
+               red_b = align256(nc * 8 + 8);
+  const size_t wtotal = fac_b + cd_b + cb_b + red_b + 256;
   if (cudaMalloc(&p->work, wtotal) != cudaSuccess) {
     cudaGetLastError();
     p->work = nullptr;
@@ -78,12 +97,15 @@ hines_status upload(hines_plan_t p, int cta_threads) {
   D.fac = w;
   D.cd = w + fac_b;
   D.cb = w + fac_b + cd_b;
-  D.red = w + fac_b + 2 * cd_b;
+  D.red = w + fac_b + cd_b + cb_b;
+  D.counter = reinterpret_cast<int32_t*>(w + fac_b + cd_b + cb_b + red_b);
+  D.n_wtasks = H.n_tasks;
   D.n_cells = H.n_cells;
   D.n_tasks = H.n_cells;
   D.cta_threads = cta_threads;
   D.n_unknowns = H.n_unknowns;
   D.n_branches = (int64_t)nb;
+  if (hines::prepare_warp_kernels(D) != cudaSuccess) return HINES_ERR_CUDA;
   return HINES_OK;
 }
 
@@ -169,6 +191,8 @@ hines_status hines_plan_info(hines_plan_t p, hines_plan_info_t* info) {
   if (!p || !info) return HINES_ERR_INVALID_ARG;
   info->n_cells = p->host.n_cells;
   info->max_levels = p->host.max_levels;
+  info->n_tasks = p->host.n_tasks;
+  info->reserved = 0;
   info->n_unknowns = p->host.n_unknowns;
   info->n_branches = (int64_t)p->host.br_first.size();
   info->workspace_bytes = p->work_bytes;
@@ -192,6 +216,16 @@ hines_status hines_plan_export(hines_plan_t p, int64_t* first, int64_t* len, int
   return HINES_OK;
 }
 
+hines_status hines_plan_export_tasks(hines_plan_t p, int64_t* cell_task, int64_t* task_order) {
+  if (!p) return HINES_ERR_INVALID_ARG;
+  const hines::HostPlan& H = p->host;
+  if (cell_task)
+    for (size_t c = 0; c < H.cell_task.size(); ++c) cell_task[c] = H.cell_task[c];
+  if (task_order)
+    for (size_t b = 0; b < H.torder.size(); ++b) task_order[b] = H.torder[b];
+  return HINES_OK;
+}
+
 hines_status hines_solve(hines_plan_t p, int32_t dtype, const void* d, const void* u, void* b_inout,
                          hines_stream_t stream) {
   hines_status st = check_plan(p);
@@ -199,10 +233,19 @@ hines_status hines_solve(hines_plan_t p, int32_t dtype, const void* d, const voi
   if (!need(p, d) || !need(p, u) || !need(p, b_inout)) return HINES_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (dtype == HINES_F64)
-    return launched(hines::launch_solve_f64(p->dev, (const double*)d, (const double*)u, (double*)b_inout, s));
+    return launched(hines::launch_warp_solve_f64(p->dev, (const double*)d, (const double*)u, (double*)b_inout, s));
   if (dtype == HINES_F32)
-    return launched(hines::launch_solve_f32(p->dev, (const float*)d, (const float*)u, (float*)b_inout, s));
+    return launched(hines::launch_warp_solve_f32(p->dev, (const float*)d, (const float*)u, (float*)b_inout, s));
   return HINES_ERR_INVALID_ARG;
+}
+
+hines_status hines_solve_compensated(hines_plan_t p, const float* d, const float* u, const float* b, double* x_out,
+                                     hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need(p, d) || !need(p, u) || !need(p, b) || !need(p, x_out)) return HINES_ERR_INVALID_ARG;
+  return launched(
+      hines::launch_warp_solve_compensated(p->dev, d, u, b, x_out, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 hines_status hines_solve_refine(hines_plan_t p, const float* d, const float* u, const float* b, double* x_out,
@@ -221,8 +264,8 @@ hines_status hines_cable_step(hines_plan_t p, const double* s, const double* g, 
   if (st != HINES_OK) return st;
   if (!need(p, s) || !need(p, g) || !need(p, u) || !need(p, V_inout)) return HINES_ERR_INVALID_ARG;
   if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
-  return launched(
-      hines::launch_cable_step(p->dev, s, g, u, V_inout, dt, E, theta, reinterpret_cast<cudaStream_t>(stream)));
+  return launched(hines::launch_warp_cable(p->dev, s, g, u, V_inout, dt, E, theta, true,
+                                           reinterpret_cast<cudaStream_t>(stream)));
 }
 
 hines_status hines_cable_solve(hines_plan_t p, const double* s, const double* g, const double* u, double* rhs_inout,
@@ -231,8 +274,8 @@ hines_status hines_cable_solve(hines_plan_t p, const double* s, const double* g,
   if (st != HINES_OK) return st;
   if (!need(p, s) || !need(p, g) || !need(p, u) || !need(p, rhs_inout)) return HINES_ERR_INVALID_ARG;
   if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
-  return launched(
-      hines::launch_cable_solve(p->dev, s, g, u, rhs_inout, dt, theta, reinterpret_cast<cudaStream_t>(stream)));
+  return launched(hines::launch_warp_cable(p->dev, s, g, u, rhs_inout, dt, 0.0, theta, false,
+                                           reinterpret_cast<cudaStream_t>(stream)));
 }
 
 hines_status hines_grad_du(hines_plan_t p, const double* lambda, const double* x, double* grad_d, double* grad_u,

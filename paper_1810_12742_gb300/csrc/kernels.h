@@ -5,6 +5,16 @@
 
 namespace hines {
 
+// Per-branch metadata in warp-task order (one entry per position of torder).
+struct __align__(16) BrMetaT {
+  int64_t first;  // natural-layout index of the proximal compartment
+  int64_t pcomp;  // natural-layout index of the parent compartment, -1 for a cell's root branch
+  int32_t len;    // compartments (1..32)
+  int32_t cbeg;   // children: positions tchild[cbeg .. cend)
+  int32_t cend;
+  int32_t ppos;   // position of the parent branch, -1 for a root branch
+};
+
 // Device copy of the host plan (pointers into one metadata allocation) and
 // the plan's workspace.
 struct DevPlan {
@@ -24,6 +34,15 @@ struct DevPlan {
   const int32_t* br_parent = nullptr;     // [nb]
   const int32_t* child_ptr = nullptr;     // [nb + 1]
   const int32_t* child = nullptr;         // [nb - n_roots]
+  // warp tasks
+  int32_t n_wtasks = 0;
+  const int32_t* task_nlvl = nullptr;     // [n_wtasks]
+  const int64_t* task_lvl_off = nullptr;  // [n_wtasks]
+  const int32_t* tlvl_ptr = nullptr;      // per task nlvl + 1 positions
+  const BrMetaT* tmeta = nullptr;         // [nb] by position
+  const int32_t* tchild = nullptr;        // child positions
+  int32_t* counter = nullptr;             // work counter (workspace)
+  int32_t grid_f64 = 1, grid_f32 = 1, grid_cable = 1, grid_comp = 1;  // persistent grid sizes
   // workspace
   void* fac = nullptr;    // n_unknowns * 8 bytes: eliminated diagonal (FP64), or two FP32 arrays
   void* cd = nullptr;     // n_branches * 8 bytes: child-to-parent diagonal contribution
@@ -31,6 +50,16 @@ struct DevPlan {
   void* red = nullptr;    // n_cells * 8 bytes: per-cell reductions
   int32_t* status = nullptr;  // device status word
 };
+
+// warp-task kernels; prepare_warp_kernels sets their shared-memory limits and
+// persistent grid sizes once per plan (outside any stream capture)
+cudaError_t prepare_warp_kernels(DevPlan& P);
+cudaError_t launch_warp_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s);
+cudaError_t launch_warp_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s);
+cudaError_t launch_warp_solve_compensated(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
+                                          cudaStream_t s);
+cudaError_t launch_warp_cable(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
+                              double dt, double E, int theta, bool rhs_from_V, cudaStream_t s);
 
 cudaError_t launch_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s);
 cudaError_t launch_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s);

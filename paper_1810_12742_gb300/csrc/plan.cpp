@@ -107,6 +107,35 @@ bool split_level(std::vector<std::vector<Br>>& cells, int32_t level) {
   return true;
 }
 
+// Cut every branch longer than `cap` into ceil(len / cap) chained pieces of
+// near-equal length (the first len % pieces pieces, counted from the proximal
+// end, are one longer).  The system is unchanged; only the schedule is.
+void cap_branches(std::vector<Br>& bs, int32_t cap) {
+  bool any = false;
+  for (auto& b : bs) any |= b.len > cap;
+  if (!any) return;
+  std::vector<Br> nb;
+  std::vector<int32_t> last_piece(bs.size());
+  for (size_t j = 0; j < bs.size(); ++j) {
+    const Br b = bs[j];
+    const int32_t pieces = (b.len + cap - 1) / cap, base = b.len / pieces, rem = b.len % pieces;
+    int64_t first = b.first;
+    int32_t parent = b.parent < 0 ? -1 : last_piece[(size_t)b.parent];
+    for (int32_t k = 0; k < pieces; ++k) {
+      Br q;
+      q.first = first;
+      q.len = base + (k < rem ? 1 : 0);
+      q.parent = parent;
+      q.level = parent < 0 ? 0 : nb[(size_t)parent].level + 1;
+      parent = (int32_t)nb.size();
+      first += q.len;
+      nb.push_back(q);
+    }
+    last_piece[j] = parent;
+  }
+  bs.swap(nb);
+}
+
 }  // namespace
 
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,
@@ -139,6 +168,7 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
   if (split_branches)
     for (int32_t level = 0; split_level(cells, level); ++level) {
     }
+  for (auto& bs : cells) cap_branches(bs, kBranchCap);
 
   // flatten to global branch ids (cell by cell, by first compartment)
   P.cell_br_off.assign((size_t)n_cells + 1, 0);
@@ -215,6 +245,82 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
   std::iota(P.task_cell.begin(), P.task_cell.end(), 0);
   std::stable_sort(P.task_cell.begin(), P.task_cell.end(),
                    [&](int32_t x, int32_t y) { return ncomp[x] > ncomp[y]; });
+
+  // warp tasks: next-fit packing of cells in the order above while every
+  // level of the task holds at most kLanes branches (Section 4)
+  std::vector<std::vector<int32_t>> task_cells;
+  std::vector<int32_t> cnt;  // branches per level of the open task
+  std::vector<int32_t> ccnt;
+  for (int32_t c : P.task_cell) {
+    const int64_t lo = P.cell_br_off[(size_t)c], hi = P.cell_br_off[(size_t)c + 1];
+    if (lo == hi) continue;  // empty cell: nothing to solve
+    ccnt.assign((size_t)P.cell_nlvl[(size_t)c], 0);
+    for (int64_t b = lo; b < hi; ++b) ccnt[(size_t)P.br_level[(size_t)b]]++;
+    bool fits = !task_cells.empty();
+    if (fits)
+      for (size_t l = 0; l < ccnt.size(); ++l)
+        if ((l < cnt.size() ? cnt[l] : 0) + ccnt[l] > kLanes) {
+          fits = false;
+          break;
+        }
+    if (!fits) {
+      task_cells.emplace_back();
+      cnt.clear();
+    }
+    task_cells.back().push_back(c);
+    if (cnt.size() < ccnt.size()) cnt.resize(ccnt.size(), 0);
+    for (size_t l = 0; l < ccnt.size(); ++l) cnt[l] += ccnt[l];
+  }
+  // largest task first (ties: order of creation)
+  std::vector<int64_t> tsize(task_cells.size(), 0);
+  for (size_t t = 0; t < task_cells.size(); ++t)
+    for (int32_t c : task_cells[t]) tsize[t] += ncomp[c];
+  std::vector<int32_t> tperm(task_cells.size());
+  std::iota(tperm.begin(), tperm.end(), 0);
+  std::stable_sort(tperm.begin(), tperm.end(), [&](int32_t x, int32_t y) { return tsize[(size_t)x] > tsize[(size_t)y]; });
+  P.n_tasks = (int32_t)task_cells.size();
+  P.cell_task.assign((size_t)n_cells, -1);
+  P.task_nlvl.resize((size_t)P.n_tasks);
+  P.task_lvl_off.resize((size_t)P.n_tasks);
+  P.torder.clear();
+  P.torder.reserve((size_t)nb);
+  P.tlvl_ptr.clear();
+  std::vector<int32_t> ids;
+  for (int32_t t = 0; t < P.n_tasks; ++t) {
+    const auto& cs = task_cells[(size_t)tperm[(size_t)t]];
+    int32_t nl = 0;
+    ids.clear();
+    for (int32_t c : cs) {
+      P.cell_task[(size_t)c] = t;
+      nl = std::max(nl, P.cell_nlvl[(size_t)c]);
+      for (int64_t b = P.cell_br_off[(size_t)c]; b < P.cell_br_off[(size_t)c + 1]; ++b) ids.push_back((int32_t)b);
+    }
+    std::stable_sort(ids.begin(), ids.end(), [&](int32_t x, int32_t y) {
+      if (P.br_level[(size_t)x] != P.br_level[(size_t)y]) return P.br_level[(size_t)x] < P.br_level[(size_t)y];
+      if (P.br_len[(size_t)x] != P.br_len[(size_t)y]) return P.br_len[(size_t)x] > P.br_len[(size_t)y];
+      if (P.br_cell[(size_t)x] != P.br_cell[(size_t)y]) return P.br_cell[(size_t)x] < P.br_cell[(size_t)y];
+      return x < y;
+    });
+    P.task_nlvl[(size_t)t] = nl;
+    P.task_lvl_off[(size_t)t] = (int64_t)P.tlvl_ptr.size();
+    const int32_t base = (int32_t)P.torder.size();
+    size_t k = 0;
+    for (int32_t l = 0; l <= nl; ++l) {
+      while (k < ids.size() && P.br_level[(size_t)ids[k]] < l) ++k;
+      P.tlvl_ptr.push_back(base + (int32_t)k);
+    }
+    P.torder.insert(P.torder.end(), ids.begin(), ids.end());
+  }
+  P.tpos.assign((size_t)nb, -1);
+  for (size_t k = 0; k < P.torder.size(); ++k) P.tpos[(size_t)P.torder[k]] = (int32_t)k;
+  P.tchild_ptr.assign((size_t)nb + 1, 0);
+  P.tchild.resize(P.child.size());
+  for (size_t k = 0; k < P.torder.size(); ++k) {
+    const int32_t b = P.torder[k];
+    P.tchild_ptr[k + 1] = P.tchild_ptr[k] + (P.child_ptr[(size_t)b + 1] - P.child_ptr[(size_t)b]);
+    int32_t w = P.tchild_ptr[k];
+    for (int32_t c = P.child_ptr[(size_t)b]; c < P.child_ptr[(size_t)b + 1]; ++c) P.tchild[(size_t)w++] = P.tpos[(size_t)P.child[(size_t)c]];
+  }
   return HINES_OK;
 }
 

@@ -30,7 +30,8 @@ HINES_F32 = 1
 
 EXPORTS = [
     "hines_plan_create", "hines_plan_destroy", "hines_plan_layout", "hines_plan_info", "hines_plan_export",
-    "hines_solve", "hines_solve_refine", "hines_cable_step", "hines_cable_solve", "hines_grad_du",
+    "hines_plan_export_tasks",
+    "hines_solve", "hines_solve_compensated", "hines_solve_refine", "hines_cable_step", "hines_cable_solve", "hines_grad_du",
     "hines_cable_adjoint_step", "hines_cable_loss_seed", "hines_plan_status", "hines_status_string",
 ]
 
@@ -47,7 +48,8 @@ class PlanOpts(ctypes.Structure):
 
 
 class PlanInfo(ctypes.Structure):
-    _fields_ = [("n_cells", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("n_unknowns", ctypes.c_int64),
+    _fields_ = [("n_cells", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("n_tasks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("n_unknowns", ctypes.c_int64),
                 ("n_branches", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("metadata_bytes", ctypes.c_int64)]
 
@@ -66,8 +68,10 @@ def lib():
             L.hines_plan_layout.argtypes = [vp, vp]
             L.hines_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
             L.hines_plan_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+            L.hines_plan_export_tasks.argtypes = [vp, vp, vp]
             L.hines_solve.argtypes = [vp, i32, vp, vp, vp, vp]
             L.hines_solve_refine.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
+            L.hines_solve_compensated.argtypes = [vp, vp, vp, vp, vp, vp]
             L.hines_cable_step.argtypes = [vp, vp, vp, vp, vp, f64, f64, i32, vp]
             L.hines_cable_solve.argtypes = [vp, vp, vp, vp, vp, f64, i32, vp]
             L.hines_grad_du.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -116,6 +120,7 @@ class Plan:
         self.n_unknowns = info.n_unknowns
         self.n_branches = info.n_branches
         self.max_levels = info.max_levels
+        self.n_tasks = info.n_tasks
         self.workspace_bytes = info.workspace_bytes
         self.metadata_bytes = info.metadata_bytes
         self.host_only = host_only
@@ -134,6 +139,13 @@ class Plan:
                                                   ("first", "len", "parent_branch", "level", "cell", "order"))),
                "hines_plan_export")
         return out
+
+    def export_tasks(self) -> dict:
+        cell_task = np.empty(self.n_cells, np.int64)
+        task_order = np.empty(self.n_branches, np.int64)
+        _check(lib().hines_plan_export_tasks(self._h, _np_ptr(cell_task), _np_ptr(task_order)),
+               "hines_plan_export_tasks")
+        return {"cell_task": cell_task, "task_order": task_order}
 
     def status(self) -> int:
         st = ctypes.c_int32(0)
@@ -186,6 +198,18 @@ def solve(plan: Plan, d, u, b):
     _check(lib().hines_solve(plan.handle, code, _dptr(d, dt, n, "d"), _dptr(u, dt, n, "u"), _dptr(b, dt, n, "b"),
                              _stream()), "hines_solve")
     return b
+
+
+def solve_compensated(plan: Plan, d, u, b, x=None):
+    """FP32 inputs, double-float (compensated FP32) elimination, FP64 solution x."""
+    torch = _torch()
+    n = plan.n_unknowns
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=b.device)
+    _check(lib().hines_solve_compensated(plan.handle, _dptr(d, torch.float32, n, "d"), _dptr(u, torch.float32, n, "u"),
+                                         _dptr(b, torch.float32, n, "b"), _dptr(x, torch.float64, n, "x"), _stream()),
+           "hines_solve_compensated")
+    return x
 
 
 def solve_refine(plan: Plan, d, u, b, x=None, steps: int = 2, relres=None):

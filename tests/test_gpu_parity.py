@@ -190,3 +190,38 @@ def test_wrong_device_arguments_rejected():
                 torch.zeros(3, dtype=torch.float64))
     with pytest.raises(ValueError):
         H.solve(plan, dev(np.zeros(4)), dev(np.zeros(4)), dev(np.zeros(4)))
+
+
+def test_solve_compensated_zoo_edge_cases():
+    ncomp, parent, c = zoo_batch(35)
+    f = {k: c[k].astype(np.float32) for k in ("d", "u", "b")}
+    for split in (False, True):
+        plan = H.Plan(ncomp, parent, split_branches=split)
+        x = H.solve_compensated(plan, *(dev(f[k], torch.float32) for k in ("d", "u", "b")))
+        ref = oracle.solve_batch(ncomp, parent, *(f[k].astype(np.float64) for k in ("d", "u", "b")))
+        assert cell_rel_err(x.cpu().numpy(), ref, plan.offsets).max() <= TOL_REFINE
+
+
+@pytest.mark.parametrize("margin,tol", [(1e-1, TOL_REFINE), (1e-3, TOL_REFINE), (1e-5, 1e-9)])
+def test_solve_compensated_margin_sweep(margin, tol):
+    """Leak margins of the mixed-precision workload: error grows with the
+    conditioning; at margin 1e-5 (Skeel condition ~5e5) the FP64 oracle itself
+    carries ~cond * 1e-16 error, so the bound there is 1e-9."""
+    w = I.WORKLOADS["uneven_mixed"]
+    cls = I.cell_classes(w)
+    cells = np.concatenate([np.nonzero(cls == 0)[0][:24], np.nonzero(cls == 1)[0][:3]])
+    pop = I.population(w, cells=cells, margin=margin)
+    f = _widened(pop)
+    plan = H.Plan(pop["ncomp"], pop["parent"])
+    x = H.solve_compensated(plan, *(dev(f[k], torch.float32) for k in ("d", "u", "b")))
+    ref = oracle.solve_batch(pop["ncomp"], pop["parent"], *(f[k].astype(np.float64) for k in ("d", "u", "b")))
+    assert cell_rel_err(x.cpu().numpy(), ref, plan.offsets).max() <= tol
+
+
+def test_solve_compensated_deterministic():
+    ncomp, parent, c = zoo_batch(36, sizes=(200, 1500))
+    f = {k: dev(c[k].astype(np.float32), torch.float32) for k in ("d", "u", "b")}
+    plan = H.Plan(ncomp, parent)
+    x1 = H.solve_compensated(plan, f["d"], f["u"], f["b"])
+    x2 = H.solve_compensated(plan, f["d"], f["u"], f["b"])
+    assert torch.equal(x1, x2)

@@ -60,11 +60,54 @@ def py_split(cells):
         level += 1
 
 
+CAP, LANES = 32, 32
+
+
+def py_cap(bs, cap=CAP):
+    """Branches longer than cap become ceil(len/cap) chained pieces; the first
+    len % pieces pieces (from the proximal end) are one longer."""
+    out, last = [], {}
+    for j, b in enumerate(bs):
+        pieces = -(-b[1] // cap)
+        base, rem = divmod(b[1], pieces)
+        parent = -1 if b[2] < 0 else last[b[2]]
+        first = b[0]
+        for k in range(pieces):
+            ln = base + (1 if k < rem else 0)
+            out.append([first, ln, parent, 0 if parent < 0 else out[parent][3] + 1])
+            parent = len(out) - 1
+            first += ln
+        last[j] = parent
+    return out
+
+
+def py_tasks(ncomp, cells, level, length):
+    """Next-fit packing of cells (largest first, ties by index) while every
+    level of a task holds at most 32 branches; tasks largest first; branches
+    of a task by level, length desc, cell, id."""
+    order = sorted(range(len(ncomp)), key=lambda c: (-ncomp[c], c))
+    tasks, cnt = [], []
+    for c in order:
+        if not cells[c]:
+            continue
+        cc = np.bincount([b[3] for b in cells[c]])
+        fits = bool(tasks) and all((cnt[l] if l < len(cnt) else 0) + cc[l] <= LANES for l in range(len(cc)))
+        if not fits:
+            tasks.append([])
+            cnt = []
+        tasks[-1].append(c)
+        cnt = [(cnt[l] if l < len(cnt) else 0) + (cc[l] if l < len(cc) else 0) for l in range(max(len(cnt), len(cc)))]
+    sizes = [sum(ncomp[c] for c in t) for t in tasks]
+    perm = sorted(range(len(tasks)), key=lambda t: (-sizes[t], t))
+    return [tasks[t] for t in perm]
+
+
 def py_plan(ncomp, parent, split=False):
     off = np.concatenate(([0], np.cumsum(ncomp))).astype(np.int64)
     cells = [py_branches(parent[off[c]:off[c + 1]]) for c in range(len(ncomp))]
     if split:
         cells = py_split(cells)
+    cells = [py_cap(bs) for bs in cells]
     first, length, pbr, level, cell, order = [], [], [], [], [], []
     base = 0
     for c, bs in enumerate(cells):
@@ -78,16 +121,34 @@ def py_plan(ncomp, parent, split=False):
         ids.sort(key=lambda g: (level[g], -length[g], g))
         order += ids
         base += len(bs)
-    return {k: np.array(v, np.int64) for k, v in
-            dict(first=first, len=length, parent_branch=pbr, level=level, cell=cell, order=order).items()}
+    out = {k: np.array(v, np.int64) for k, v in
+           dict(first=first, len=length, parent_branch=pbr, level=level, cell=cell, order=order).items()}
+    tasks = py_tasks(list(ncomp), cells, level, length)
+    cell_task = np.full(len(ncomp), -1, np.int64)
+    base_of = np.concatenate(([0], np.cumsum([len(bs) for bs in cells]))).astype(np.int64)
+    torder = []
+    for t, cs in enumerate(tasks):
+        ids = []
+        for c in cs:
+            cell_task[c] = t
+            ids += list(range(base_of[c], base_of[c + 1]))
+        ids.sort(key=lambda g: (level[g], -length[g], cell[g], g))
+        torder += ids
+    out["cell_task"] = cell_task
+    out["task_order"] = np.array(torder, np.int64)
+    out["n_tasks"] = len(tasks)
+    return out
 
 
 def _compare(ncomp, parent, split):
     plan = H.Plan(ncomp, parent, split_branches=split, host_only=True)
     got = plan.export()
+    got.update(plan.export_tasks())
     ref = py_plan(np.asarray(ncomp), np.asarray(parent), split)
+    assert plan.n_tasks == ref.pop("n_tasks")
     for k in ref:
         assert np.array_equal(got[k], ref[k]), k
+    assert got["len"].max(initial=0) <= CAP
     assert plan.n_unknowns == int(np.sum(ncomp))
     return got
 
@@ -155,6 +216,23 @@ def test_split_shortens_long_branches():
     assert b.n_branches > a.n_branches
     assert eb["len"].max() <= ea["len"].max()
     assert b.max_levels > a.max_levels
+
+
+def test_tasks_respect_lane_rule_and_cover_cells():
+    w = I.WORKLOADS["uneven_steps"]
+    cls = I.cell_classes(w)
+    cells = np.concatenate([np.nonzero(cls == 0)[0][:40], np.nonzero(cls == 1)[0][:2]])
+    ncomp, parent = I.population_trees(w, cells)
+    plan = H.Plan(ncomp, parent, host_only=True)
+    e = plan.export()
+    t = plan.export_tasks()
+    assert (t["cell_task"] >= 0).all() and plan.n_tasks < len(cells)
+    assert sorted(t["task_order"].tolist()) == list(range(plan.n_branches))
+    for task in range(plan.n_tasks):
+        members = np.nonzero(t["cell_task"] == task)[0]
+        lv = e["level"][np.isin(e["cell"], members)]
+        if len(members) > 1:
+            assert np.bincount(lv).max() <= 32
 
 
 def test_planner_time_is_linear():
