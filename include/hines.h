@@ -226,6 +226,13 @@ hines_status hines_cable_adjoint_step(hines_plan_t plan, const double *lambda, c
                                       double *vbar_out, hines_stream_t stream);
 
 /*
+ * Rollout loss term: loss_cells[c] += (V[root of c] - target[c])^2 for every
+ * cell.  Device arrays (V: n_unknowns; target, loss_cells: n_cells).
+ */
+hines_status hines_cable_loss_accumulate(hines_plan_t plan, const double *V, const double *target,
+                                         double *loss_cells, hines_stream_t stream);
+
+/*
  * Loss seed: vbar[root of c] += 2 (V[root of c] - target[c]) for every cell.
  * Device arrays; used for the last step of a rollout.
  */

@@ -310,6 +310,15 @@ hines_status hines_cable_loss_seed(hines_plan_t p, const double* V, const double
   return launched(hines::launch_cable_loss_seed(p->dev, V, target, vbar, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+hines_status hines_cable_loss_accumulate(hines_plan_t p, const double* V, const double* target, double* loss_cells,
+                                         hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need(p, V) || ((!target || !loss_cells) && p->host.n_cells > 0)) return HINES_ERR_INVALID_ARG;
+  return launched(
+      hines::launch_cable_loss_accumulate(p->dev, V, target, loss_cells, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 hines_status hines_plan_status(hines_plan_t p, int32_t* status_out) {
   hines_status st = check_plan(p);
   if (st != HINES_OK) return st;

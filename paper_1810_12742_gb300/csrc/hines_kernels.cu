@@ -351,6 +351,17 @@ __global__ void k_cable_loss_seed(DevPlan P, const double* __restrict__ V, const
   if (P.cell_off[c + 1] > lo) vbar[lo] += 2.0 * (V[lo] - target[c]);
 }
 
+__global__ void k_cable_loss_accumulate(DevPlan P, const double* __restrict__ V, const double* __restrict__ target,
+                                        double* __restrict__ loss) {
+  const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.n_cells) return;
+  const int64_t lo = P.cell_off[c];
+  if (P.cell_off[c + 1] > lo) {
+    const double e = V[lo] - target[c];
+    loss[c] += e * e;
+  }
+}
+
 int grid_for_branches(const DevPlan& P) {
   const int64_t warps = P.n_branches;
   const int64_t blocks = (warps * 32 + 255) / 256;
@@ -413,6 +424,13 @@ cudaError_t launch_cable_adjoint_step(const DevPlan& P, const double* lam, const
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !add_loss) return e;
   return launch_cable_loss_seed(P, Vkm1, target, vbar, s);
+}
+
+cudaError_t launch_cable_loss_accumulate(const DevPlan& P, const double* V, const double* target, double* loss,
+                                         cudaStream_t s) {
+  if (P.n_cells == 0) return cudaSuccess;
+  k_cable_loss_accumulate<<<(P.n_cells + 255) / 256, 256, 0, s>>>(P, V, target, loss);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cable_loss_seed(const DevPlan& P, const double* V, const double* target, double* vbar,

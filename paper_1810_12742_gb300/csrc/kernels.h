@@ -75,6 +75,8 @@ cudaError_t launch_cable_adjoint_step(const DevPlan& P, const double* lam, const
                                       const double* sv, const double* g, const double* target, double dt, double E,
                                       int theta, int add_loss, double* grad_g, double* grad_a, double* vbar,
                                       cudaStream_t s);
+cudaError_t launch_cable_loss_accumulate(const DevPlan& P, const double* V, const double* target, double* loss,
+                                         cudaStream_t s);
 cudaError_t launch_cable_loss_seed(const DevPlan& P, const double* V, const double* target, double* vbar,
                                    cudaStream_t s);
 

@@ -32,7 +32,8 @@ EXPORTS = [
     "hines_plan_create", "hines_plan_destroy", "hines_plan_layout", "hines_plan_info", "hines_plan_export",
     "hines_plan_export_tasks",
     "hines_solve", "hines_solve_compensated", "hines_solve_refine", "hines_cable_step", "hines_cable_solve", "hines_grad_du",
-    "hines_cable_adjoint_step", "hines_cable_loss_seed", "hines_plan_status", "hines_status_string",
+    "hines_cable_adjoint_step", "hines_cable_loss_seed", "hines_cable_loss_accumulate", "hines_plan_status",
+    "hines_status_string",
 ]
 
 
@@ -77,6 +78,7 @@ def lib():
             L.hines_grad_du.argtypes = [vp, vp, vp, vp, vp, vp]
             L.hines_cable_adjoint_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, f64, f64, i32, i32, vp, vp, vp, vp]
             L.hines_cable_loss_seed.argtypes = [vp, vp, vp, vp, vp]
+            L.hines_cable_loss_accumulate.argtypes = [vp, vp, vp, vp, vp]
             L.hines_plan_status.argtypes = [vp, ctypes.POINTER(i32)]
             L.hines_status_string.argtypes = [i32]
             L.hines_status_string.restype = ctypes.c_char_p

@@ -1,0 +1,126 @@
+"""Time stepping, CUDA-graph capture and adjoints on top of the C-ABI.
+
+Every numerical step runs in libhines kernels; this module only orders the
+calls, captures them in a CUDA graph and keeps the checkpoints.
+
+* ``CableStepper``: K fused rebuild + solve steps of the passive cable
+  (hines_cable_step) captured once in a CUDA graph and replayed.
+* ``cable_rollout`` / ``cable_rollout_grad``: loss
+  L = sum over cells and steps of (V_root^k - target)^2 and its gradient with
+  respect to the leak conductance g and the axial coefficients a (u = -a),
+  with the states checkpointed every ``checkpoint_every`` steps and each
+  segment recomputed during the reverse sweep.  The matrix is symmetric, so
+  the adjoint of a step is one more Hines solve (hines_cable_solve).
+* ``HinesSolve`` and ``CableRollout``: torch.autograd.Function wrappers.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import hines as H
+
+
+class CableStepper:
+    """``steps`` implicit-Euler steps of the passive cable, captured in one CUDA
+    graph; ``replay()`` advances V in place by ``steps`` steps."""
+
+    def __init__(self, plan: H.Plan, s, g, u, V, dt: float, E: float, theta: int = 1, steps: int = 1000):
+        self.plan, self.args = plan, (s, g, u, V, dt, E, theta)
+        self.steps = steps
+        # one eager step on a scratch copy creates the kernels' resources before capture
+        tmp = V.clone()
+        H.cable_step(plan, s, g, u, tmp, dt, E, theta)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            for _ in range(steps):
+                H.cable_step(plan, s, g, u, V, dt, E, theta)
+
+    def replay(self):
+        self.graph.replay()
+
+
+def cable_rollout(plan: H.Plan, s, g, u, V0, target, steps: int, dt: float, E: float, theta: int = 1,
+                  checkpoint_every: int = 20):
+    """Forward rollout.  Returns (loss per cell, checkpoints) where
+    checkpoints[j] is V at step j * checkpoint_every."""
+    V = V0.clone()
+    loss = torch.zeros(plan.n_cells, dtype=torch.float64, device=V.device)
+    ckpt = [V0.clone()]
+    for k in range(1, steps + 1):
+        H.cable_step(plan, s, g, u, V, dt, E, theta)
+        H.lib().hines_cable_loss_accumulate(plan.handle, H._dptr(V, torch.float64, plan.n_unknowns, "V"),
+                                            H._dptr(target, torch.float64, plan.n_cells, "target"),
+                                            H._dptr(loss, torch.float64, plan.n_cells, "loss"), H._stream())
+        if k % checkpoint_every == 0 and k < steps:
+            ckpt.append(V.clone())
+    return loss, ckpt, V
+
+
+def cable_rollout_grad(plan: H.Plan, s, g, u, target, steps: int, dt: float, E: float, theta: int,
+                       checkpoint_every: int, ckpt, V_last):
+    """Reverse sweep with segment recomputation.  Returns (dL/dg, dL/da)."""
+    n = plan.n_unknowns
+    dev = s.device
+    grad_g = torch.zeros(n, dtype=torch.float64, device=dev)
+    grad_a = torch.zeros(n, dtype=torch.float64, device=dev)
+    vbar = torch.zeros(n, dtype=torch.float64, device=dev)
+    H.cable_loss_seed(plan, V_last, target, vbar)
+    lam = torch.empty_like(vbar)
+    nseg = (steps + checkpoint_every - 1) // checkpoint_every
+    for seg in range(nseg - 1, -1, -1):
+        k0 = seg * checkpoint_every
+        k1 = min(steps, k0 + checkpoint_every)
+        states = [ckpt[seg].clone()]
+        for _ in range(k0, k1):
+            V = states[-1].clone()
+            H.cable_step(plan, s, g, u, V, dt, E, theta)
+            states.append(V)
+        for k in range(k1, k0, -1):
+            lam.copy_(vbar)
+            H.cable_solve(plan, s, g, u, lam, dt, theta)
+            H.cable_adjoint_step(plan, lam, states[k - k0], states[k - 1 - k0], s, g, target, dt, E, theta,
+                                 int(k - 1 >= 1), grad_g, grad_a, vbar)
+    return grad_g, grad_a
+
+
+class CableRollout(torch.autograd.Function):
+    """loss = CableRollout.apply(g, a, plan, s, V0, target, steps, dt, E, theta, checkpoint_every)"""
+
+    @staticmethod
+    def forward(ctx, g, a, plan, s, V0, target, steps, dt, E, theta=1, checkpoint_every=20):
+        u = torch.neg(a)
+        loss, ckpt, V_last = cable_rollout(plan, s, g, u, V0, target, steps, dt, E, theta, checkpoint_every)
+        ctx.plan, ctx.cfg = plan, (steps, dt, E, theta, checkpoint_every)
+        ctx.ckpt, ctx.V_last = ckpt, V_last
+        ctx.save_for_backward(g, u, s, target)
+        return loss.sum()
+
+    @staticmethod
+    def backward(ctx, gL):
+        g, u, s, target = ctx.saved_tensors
+        steps, dt, E, theta, ce = ctx.cfg
+        grad_g, grad_a = cable_rollout_grad(ctx.plan, s, g, u, target, steps, dt, E, theta, ce, ctx.ckpt, ctx.V_last)
+        return gL * grad_g, gL * grad_a, None, None, None, None, None, None, None, None, None
+
+
+class HinesSolve(torch.autograd.Function):
+    """x = HinesSolve.apply(plan, d, u, b): FP64 solve with its adjoint.
+    Backward: lambda = A^{-1} xbar (a second solve, A symmetric); db = lambda,
+    dd = -lambda x, du_i = -(lambda_i x_p(i) + lambda_p(i) x_i)."""
+
+    @staticmethod
+    def forward(ctx, plan, d, u, b):
+        x = b.detach().clone()
+        H.solve(plan, d.detach(), u.detach(), x)
+        ctx.plan = plan
+        ctx.save_for_backward(d, u, x)
+        return x
+
+    @staticmethod
+    def backward(ctx, xbar):
+        d, u, x = ctx.saved_tensors
+        lam = xbar.detach().contiguous().clone()
+        H.solve(ctx.plan, d.detach(), u.detach(), lam)
+        gd, gu = H.grad_du(ctx.plan, lam, x)
+        return None, gd, gu, lam
