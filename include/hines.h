@@ -239,6 +239,32 @@ hines_status hines_cable_loss_accumulate(hines_plan_t plan, const double *V, con
 hines_status hines_cable_loss_seed(hines_plan_t plan, const double *V, const double *target, double *vbar,
                                    hines_stream_t stream);
 
+/*
+ * Allocation-free FP64 solve, for callers that may not allocate device
+ * memory (a host runtime whose device allocator is fixed at start-up, a
+ * memory pool that forbids new allocations, code that must not change the
+ * process's device footprint).  Such callers cannot create a plan, because
+ * plan creation allocates; this call needs none.  It solves every cell of the
+ * batch in place with one GPU thread per cell, and keeps the eliminated
+ * diagonal in a fixed device array inside the library (16 MiB per GPU that
+ * loads the library, held until the process exits).  No paper counterpart:
+ * it is the serial algorithm of Listing 2 with its scratch preallocated.
+ *   n_unknowns    total compartments, 0 .. 2,097,152 (larger: HINES_ERR_INVALID_ARG)
+ *   n_cells       >= 0
+ *   cell_offsets  device int64[n_cells + 1], natural-layout offsets
+ *   parent        device int32[n_unknowns], cell-local parent arrays
+ *   d, u          device double[n_unknowns], not modified
+ *   b_inout       device double[n_unknowns]: right-hand side in, solution out
+ * Stream-ordered.  A cell whose offsets or parent array are invalid is left
+ * with NaN in b_inout.  The first call on a device looks up the device
+ * address of the scratch array, so make it before any stream capture.  All
+ * calls share the scratch array: calls whose work may overlap on the GPU
+ * (unordered streams) race on it.
+ */
+hines_status hines_solve_f64_noalloc(int64_t n_unknowns, int32_t n_cells, const int64_t *cell_offsets,
+                                     const int32_t *parent, const double *d, const double *u, double *b_inout,
+                                     hines_stream_t stream);
+
 /* Read (synchronously) and clear the plan's device status word. */
 hines_status hines_plan_status(hines_plan_t plan, int32_t *status_out);
 

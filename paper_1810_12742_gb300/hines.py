@@ -34,6 +34,7 @@ EXPORTS = [
     "hines_solve", "hines_solve_compensated", "hines_solve_refine", "hines_cable_step", "hines_cable_solve", "hines_grad_du",
     "hines_cable_adjoint_step", "hines_cable_loss_seed", "hines_cable_loss_accumulate", "hines_plan_status",
     "hines_status_string",
+    "hines_solve_f64_noalloc",
 ]
 
 
@@ -80,6 +81,7 @@ def lib():
             L.hines_cable_loss_seed.argtypes = [vp, vp, vp, vp, vp]
             L.hines_cable_loss_accumulate.argtypes = [vp, vp, vp, vp, vp]
             L.hines_plan_status.argtypes = [vp, ctypes.POINTER(i32)]
+            L.hines_solve_f64_noalloc.argtypes = [ctypes.c_int64, i32, vp, vp, vp, vp, vp, vp]
             L.hines_status_string.argtypes = [i32]
             L.hines_status_string.restype = ctypes.c_char_p
             for name in EXPORTS:
