@@ -67,7 +67,10 @@ typedef struct {
                               inspected with hines_plan_info / hines_plan_export but not solved */
   int32_t split_branches;  /* 1: split branches longer than their level's mean (Section 6) */
   int32_t cta_threads;     /* threads per CTA of the level-synchronous kernels (0: 256) */
-  int32_t reserved[5];     /* must be zero */
+  int32_t sort_by_length;  /* 1: within a level of a warp task, order branches by length (descending;
+                              Section 4, Fig. 4.1); 0: by memory order, so that a chunk of 32
+                              branches of a breadth-first numbered cell is one contiguous range */
+  int32_t reserved[4];     /* must be zero */
 } hines_plan_opts;
 
 /* Plan summary. */
@@ -94,7 +97,7 @@ typedef struct {
  * (maximal unbranched runs: compartment i starts a branch when i = 0,
  * p[i] != i-1, or p[i] has two or more children), optionally splits branches
  * longer than their level's mean (Section 6), cuts every branch longer than
- * 32 compartments into near-equal chained pieces, assigns levels (number of
+ * 16 compartments into near-equal chained pieces, assigns levels (number of
  * ancestor branches), orders the branches of every level by length
  * (descending, ties by branch index; Section 4, Fig. 4.1), packs cells into
  * warp tasks (Section 4's greedy rule with the 32 lanes of a warp: cells are
@@ -129,13 +132,21 @@ hines_status hines_plan_export(hines_plan_t plan, int64_t *first, int64_t *len, 
                                int64_t *level, int64_t *cell, int64_t *order);
 
 /*
- * Copy the warp-task schedule to host arrays (NULL skips an array):
- *   cell_task[n_cells]  task of each cell (-1 for a cell without compartments)
- *   task_order[nb]      branches in processing order: task by task (largest
- *        task first), level by level from 0, within a level by length
- *        descending, then cell, then branch index
+ * Copy the warp-task schedule to host arrays (NULL skips an array).  A cell of
+ * at most 4096 compartments is one unit; a larger cell is cut into its top
+ * part (the branches whose subtree holds more than 4096 compartments) and one
+ * unit per subtree hanging below the top part.  Units of one kind are packed
+ * into tasks, largest first, while every level (counted from each unit's root
+ * branch) holds at most 32 branches (Section 4's rule with 32 lanes).
+ *   branch_task[nb]  task of each branch
+ *   branch_kind[nb]  kind of the branch's unit: 0 whole cell, 1 subtree, 2 top part
+ *   task_order[nb]   branches in processing order: tasks whole-cell, then
+ *        subtree, then top kind, each largest first; within a task by level
+ *        from the unit roots, then cell, then branch index (with
+ *        sort_by_length: by length descending first)
  */
-hines_status hines_plan_export_tasks(hines_plan_t plan, int64_t *cell_task, int64_t *task_order);
+hines_status hines_plan_export_tasks(hines_plan_t plan, int64_t *branch_task, int64_t *branch_kind,
+                                     int64_t *task_order);
 
 /*
  * Solve A x = b for every cell (Section 2, Listing 2), in place.

@@ -1,0 +1,182 @@
+// Device helpers shared by the solve kernels (internal to libhines).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace hines {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSlots = 1024;  // 32 lanes x 32 steps
+
+__device__ __forceinline__ int sidx(int k, int j) { return (k << 5) + (j ^ (k & 31)); }
+
+// ---- asynchronous global -> shared copies (LDGSTS) --------------------------
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <typename T>
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+  if constexpr (sizeof(T) == 8)
+    cp_async8(smem, gmem);
+  else
+    cp_async4(smem, gmem);
+}
+
+// ---- reciprocals -------------------------------------------------------------
+// FP64: hardware approximation of the high word, then two Newton steps.
+__device__ __forceinline__ double rcp_t(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ float rcp_t(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// ---- double-float arithmetic from FP32 error-free transformations -------------
+// A value is an unevaluated pair hi + lo; every product and sum below uses the
+// _rn intrinsics so the compiler cannot contract them into FMAs, which would
+// break the exactness the transformations rely on.
+struct ff {
+  float h, l;
+};
+__device__ __forceinline__ ff ff_renorm(float h, float l) {  // fast two-sum, |h| >= |l|
+  const float s = __fadd_rn(h, l);
+  return {s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+// x - (yh + yl), two-sum on the leading parts
+__device__ __forceinline__ ff ff_sub(ff x, float yh, float yl) {
+  const float s = __fsub_rn(x.h, yh);
+  const float bb = __fsub_rn(s, x.h);
+  const float e = __fadd_rn(__fsub_rn(x.h, __fsub_rn(s, bb)), __fsub_rn(-yh, bb));
+  return ff_renorm(s, __fadd_rn(e, __fsub_rn(x.l, yl)));
+}
+// x - (yh + yl) when |x| >= |yh| (the diagonal chain of a diagonally dominant
+// matrix: d_{i-1} > u_i^2 / d'_i), fast two-sum on the leading parts
+__device__ __forceinline__ ff ff_sub_dom(float x, float yh, float yl) {
+  const float s = __fsub_rn(x, yh);
+  const float e = __fsub_rn(__fsub_rn(x, s), yh);
+  return ff_renorm(s, __fsub_rn(e, yl));
+}
+// f = u / d for an FP32 u
+__device__ __forceinline__ ff ff_div_f(float u, ff d) {
+  const float r = rcp_t(d.h);
+  const float F = __fmul_rn(u, r);
+  float t = fmaf(-F, d.h, u);
+  t = fmaf(-F, d.l, t);
+  return ff_renorm(F, __fmul_rn(t, r));
+}
+// n / d
+__device__ __forceinline__ ff ff_div(ff n, ff d) {
+  const float r = rcp_t(d.h);
+  const float X = __fmul_rn(n.h, r);
+  float t = fmaf(-X, d.h, n.h);
+  t = __fadd_rn(t, n.l);
+  t = fmaf(-X, d.l, t);
+  return ff_renorm(X, __fmul_rn(t, r));
+}
+// f * u for an FP32 u (exact leading product plus the lo term)
+__device__ __forceinline__ ff ff_mul_f(ff f, float u) {
+  const float P = __fmul_rn(f.h, u);
+  float p = fmaf(f.h, u, -P);
+  p = fmaf(f.l, u, p);
+  return {P, p};
+}
+// f * b
+__device__ __forceinline__ ff ff_mul(ff f, ff b) {
+  const float Q = __fmul_rn(f.h, b.h);
+  float q = fmaf(f.h, b.h, -Q);
+  q = fmaf(f.h, b.l, q);
+  q = fmaf(f.l, b.h, q);
+  return {Q, q};
+}
+
+// hi + lo rounded to FP64 with integer operations on the bit pattern (no FP64
+// pipe): hi is widened exactly by re-biasing its exponent, lo is scaled to
+// units of the last place of that double and added to the bit pattern.  Rare
+// cases (tiny or huge hi, large lo, a sum crossing below hi's binade) take an
+// FP64 path kept out of line, so the compiler cannot evaluate it
+// speculatively for every element.
+static __device__ __noinline__ double ff_to_double_slow(float hi, float lo) { return (double)hi + (double)lo; }
+
+__device__ __forceinline__ double ff_to_double(float hi, float lo) {
+  const uint32_t hb = __float_as_uint(hi);
+  const uint32_t ex = (hb >> 23) & 0xFFu;
+  const float q = __fmul_rn(lo, __uint_as_float((306u - min(max(ex, 64u), 253u)) << 23));  // lo / ulp_double(hi)
+  int32_t k = __float2int_rn(q);
+  if (hb & 0x80000000u) k = -k;  // bits hold the magnitude
+  const bool slow = ex < 64u || ex > 253u || !(fabsf(q) < 1073741824.0f) || (k < 0 && (hb & 0x7FFFFFu) == 0u);
+  if (slow) return ff_to_double_slow(hi, lo);
+  const uint64_t db = ((uint64_t)(hb & 0x80000000u) << 32) | ((uint64_t)(ex + 896u) << 52) |
+                      ((uint64_t)(hb & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)(db + (uint64_t)(int64_t)k));
+}
+
+}  // namespace dev
+}  // namespace hines
+
+namespace hines {
+namespace dev {
+
+// ---- bulk copies through the tensor memory accelerator (TMA) ---------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// make initialised mbarriers and earlier generic shared-memory accesses visible
+// to the asynchronous (TMA) proxy
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// global -> shared bulk copy; src, dst 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with the given parity; gives up after a bounded number of
+// polls (each poll may suspend the thread for a while), records
+// HINES_ERR_TIMEOUT in the status word and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int32_t* status) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicMax(status, 5 /* HINES_ERR_TIMEOUT */);
+  return false;
+}
+
+}  // namespace dev
+}  // namespace hines

@@ -1,6 +1,8 @@
 // C-ABI of libhines: plan lifetime, argument checks and kernel dispatch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -34,18 +36,26 @@ hines_status upload(hines_plan_t p, int cta_threads) {
     const void** dst;
   };
   hines::DevPlan& D = p->dev;
-  // per-branch metadata in warp-task order
+  // per-branch metadata in task order
   std::vector<hines::BrMetaT> tmeta(H.torder.size());
   for (size_t k = 0; k < H.torder.size(); ++k) {
     const int32_t b = H.torder[k];
     hines::BrMetaT& m = tmeta[k];
     m.first = H.br_first[(size_t)b];
-    m.len = H.br_len[(size_t)b];
+    m.len = (int16_t)H.br_len[(size_t)b];
     const int32_t pb = H.br_parent[(size_t)b];
     m.pcomp = pb < 0 ? -1 : H.br_first[(size_t)pb] + H.br_len[(size_t)pb] - 1;
     m.ppos = pb < 0 ? -1 : H.tpos[(size_t)pb];
-    m.cbeg = H.tchild_ptr[k];
-    m.cend = H.tchild_ptr[k + 1];
+    const int32_t cb = H.tchild_ptr[k], ce = H.tchild_ptr[k + 1];
+    m.nchild = (int16_t)(ce - cb);
+    int32_t lo = INT32_MAX, hi = -1;
+    for (int32_t q = cb; q < ce; ++q) {
+      lo = std::min(lo, H.tchild[(size_t)q]);
+      hi = std::max(hi, H.tchild[(size_t)q]);
+    }
+    m.ccontig = (int16_t)(ce > cb && hi - lo + 1 == ce - cb);
+    m.cpos = m.ccontig ? lo : cb;
+    m.pad = 0;
   }
   std::vector<Item> items = {
       {tmeta.data(), tmeta.size() * sizeof(hines::BrMetaT), (const void**)&D.tmeta},
@@ -53,6 +63,7 @@ hines_status upload(hines_plan_t p, int cta_threads) {
       {H.task_lvl_off.data(), H.task_lvl_off.size() * 8, (const void**)&D.task_lvl_off},
       {H.tlvl_ptr.data(), H.tlvl_ptr.size() * 4, (const void**)&D.tlvl_ptr},
       {H.tchild.data(), H.tchild.size() * 4, (const void**)&D.tchild},
+      {H.phase_entry.data(), H.phase_entry.size() * 4, (const void**)&D.phase_entry},
       {H.cell_off.data(), H.cell_off.size() * 8, (const void**)&D.cell_off},
       {H.task_cell.data(), H.task_cell.size() * 4, (const void**)&D.task_cell},
       {H.cell_nlvl.data(), H.cell_nlvl.size() * 4, (const void**)&D.cell_nlvl},
@@ -85,8 +96,8 @@ hines_status upload(hines_plan_t p, int cta_threads) {
   }
   const size_t n = (size_t)H.n_unknowns, nb = H.br_first.size(), nc = (size_t)H.n_cells;
   const size_t fac_b = align256(n * 8 + 8), cd_b = align256(nb * 16 + 16), cb_b = align256(nb * 8 + 8),
-               red_b = align256(nc * 8 + 8);
-  const size_t wtotal = fac_b + cd_b + cb_b + red_b + 256;
+               ds_b = align256(nb * 16 + 16), xl_b = align256(nb * 8 + 8), red_b = align256(nc * 8 + 8);
+  const size_t wtotal = fac_b + cd_b + cb_b + ds_b + xl_b + red_b + 256;
   if (cudaMalloc(&p->work, wtotal) != cudaSuccess) {
     cudaGetLastError();
     p->work = nullptr;
@@ -95,17 +106,26 @@ hines_status upload(hines_plan_t p, int cta_threads) {
   p->work_bytes = (int64_t)wtotal;
   char* w = static_cast<char*>(p->work);
   D.fac = w;
-  D.cd = w + fac_b;
-  D.cb = w + fac_b + cd_b;
-  D.red = w + fac_b + cd_b + cb_b;
-  D.counter = reinterpret_cast<int32_t*>(w + fac_b + cd_b + cb_b + red_b);
+  w += fac_b;
+  D.cd = w;
+  w += cd_b;
+  D.cb = w;
+  w += cb_b;
+  D.dstate = w;
+  w += ds_b;
+  D.xlast = w;
+  w += xl_b;
+  D.red = w;
+  w += red_b;
+  D.counter = reinterpret_cast<int32_t*>(w);
   D.n_wtasks = H.n_tasks;
+  for (int k = 0; k < 4; ++k) D.phase_off[k] = H.phase_off.empty() ? 0 : H.phase_off[(size_t)k];
   D.n_cells = H.n_cells;
   D.n_tasks = H.n_cells;
   D.cta_threads = cta_threads;
   D.n_unknowns = H.n_unknowns;
   D.n_branches = (int64_t)nb;
-  if (hines::prepare_warp_kernels(D) != cudaSuccess) return HINES_ERR_CUDA;
+  if (hines::prepare_unit_kernels(D) != cudaSuccess) return HINES_ERR_CUDA;
   return HINES_OK;
 }
 
@@ -132,7 +152,7 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
   hines_plan_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  for (int k = 0; k < 5; ++k)
+  for (int k = 0; k < 4; ++k)
     if (o.reserved[k] != 0) return HINES_ERR_INVALID_ARG;
   if (o.cta_threads == 0) o.cta_threads = 256;
   if (o.cta_threads < 32 || o.cta_threads > 1024 || (o.cta_threads % 32) != 0) return HINES_ERR_INVALID_ARG;
@@ -140,7 +160,7 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
   if (!p) return HINES_ERR_OOM;
   int rc;
   try {
-    rc = hines::build_host_plan(n_cells, ncomp, parent, o.split_branches, p->host);
+    rc = hines::build_host_plan(n_cells, ncomp, parent, o.split_branches, o.sort_by_length, p->host);
   } catch (const std::bad_alloc&) {
     rc = HINES_ERR_OOM;
   }
@@ -216,11 +236,13 @@ hines_status hines_plan_export(hines_plan_t p, int64_t* first, int64_t* len, int
   return HINES_OK;
 }
 
-hines_status hines_plan_export_tasks(hines_plan_t p, int64_t* cell_task, int64_t* task_order) {
+hines_status hines_plan_export_tasks(hines_plan_t p, int64_t* branch_task, int64_t* branch_kind, int64_t* task_order) {
   if (!p) return HINES_ERR_INVALID_ARG;
   const hines::HostPlan& H = p->host;
-  if (cell_task)
-    for (size_t c = 0; c < H.cell_task.size(); ++c) cell_task[c] = H.cell_task[c];
+  for (size_t b = 0; b < H.br_task.size(); ++b) {
+    if (branch_task) branch_task[b] = H.br_task[b];
+    if (branch_kind) branch_kind[b] = H.br_kind[b];
+  }
   if (task_order)
     for (size_t b = 0; b < H.torder.size(); ++b) task_order[b] = H.torder[b];
   return HINES_OK;
@@ -233,9 +255,9 @@ hines_status hines_solve(hines_plan_t p, int32_t dtype, const void* d, const voi
   if (!need(p, d) || !need(p, u) || !need(p, b_inout)) return HINES_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (dtype == HINES_F64)
-    return launched(hines::launch_warp_solve_f64(p->dev, (const double*)d, (const double*)u, (double*)b_inout, s));
+    return launched(hines::launch_unit_solve_f64(p->dev, (const double*)d, (const double*)u, (double*)b_inout, s));
   if (dtype == HINES_F32)
-    return launched(hines::launch_warp_solve_f32(p->dev, (const float*)d, (const float*)u, (float*)b_inout, s));
+    return launched(hines::launch_unit_solve_f32(p->dev, (const float*)d, (const float*)u, (float*)b_inout, s));
   return HINES_ERR_INVALID_ARG;
 }
 
@@ -245,7 +267,7 @@ hines_status hines_solve_compensated(hines_plan_t p, const float* d, const float
   if (st != HINES_OK) return st;
   if (!need(p, d) || !need(p, u) || !need(p, b) || !need(p, x_out)) return HINES_ERR_INVALID_ARG;
   return launched(
-      hines::launch_warp_solve_compensated(p->dev, d, u, b, x_out, reinterpret_cast<cudaStream_t>(stream)));
+      hines::launch_unit_solve_compensated(p->dev, d, u, b, x_out, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 hines_status hines_solve_refine(hines_plan_t p, const float* d, const float* u, const float* b, double* x_out,
@@ -264,7 +286,7 @@ hines_status hines_cable_step(hines_plan_t p, const double* s, const double* g, 
   if (st != HINES_OK) return st;
   if (!need(p, s) || !need(p, g) || !need(p, u) || !need(p, V_inout)) return HINES_ERR_INVALID_ARG;
   if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
-  return launched(hines::launch_warp_cable(p->dev, s, g, u, V_inout, dt, E, theta, true,
+  return launched(hines::launch_unit_cable(p->dev, s, g, u, V_inout, dt, E, theta, true,
                                            reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -274,7 +296,7 @@ hines_status hines_cable_solve(hines_plan_t p, const double* s, const double* g,
   if (st != HINES_OK) return st;
   if (!need(p, s) || !need(p, g) || !need(p, u) || !need(p, rhs_inout)) return HINES_ERR_INVALID_ARG;
   if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
-  return launched(hines::launch_warp_cable(p->dev, s, g, u, rhs_inout, dt, 0.0, theta, false,
+  return launched(hines::launch_unit_cable(p->dev, s, g, u, rhs_inout, dt, 0.0, theta, false,
                                            reinterpret_cast<cudaStream_t>(stream)));
 }
 

@@ -5,26 +5,29 @@
 
 namespace hines {
 
-// Per-branch metadata in warp-task order (one entry per position of torder).
+// Per-branch metadata in task order (one entry per position of torder).
 struct __align__(16) BrMetaT {
-  int64_t first;  // natural-layout index of the proximal compartment
-  int64_t pcomp;  // natural-layout index of the parent compartment, -1 for a cell's root branch
-  int32_t len;    // compartments (1..32)
-  int32_t cbeg;   // children: positions tchild[cbeg .. cend)
-  int32_t cend;
-  int32_t ppos;   // position of the parent branch, -1 for a root branch
+  int64_t first;    // natural-layout index of the proximal compartment
+  int64_t pcomp;    // natural-layout index of the parent compartment, -1 for a cell's root branch
+  int32_t ppos;     // position of the parent branch, -1 for a cell's root branch
+  int32_t cpos;     // children: first child position if contiguous, else first index into tchild
+  int16_t len;      // compartments (1..16)
+  int16_t nchild;   // children
+  int16_t ccontig;  // 1: the children are positions cpos .. cpos + nchild - 1
+  int16_t pad;
 };
 
 // Device copy of the host plan (pointers into one metadata allocation) and
 // the plan's workspace.
 struct DevPlan {
   int32_t n_cells = 0;
-  int32_t n_tasks = 0;
+  int32_t n_tasks = 0;          // cells, for the CTA-per-cell kernels
   int32_t cta_threads = 256;
   int64_t n_unknowns = 0;
   int64_t n_branches = 0;
+  // CTA-per-cell level-synchronous kernels
   const int64_t* cell_off = nullptr;      // [n_cells + 1]
-  const int32_t* task_cell = nullptr;     // [n_tasks]
+  const int32_t* task_cell = nullptr;     // [n_cells] cells, most compartments first
   const int32_t* cell_nlvl = nullptr;     // [n_cells]
   const int64_t* cell_lvl_off = nullptr;  // [n_cells]
   const int32_t* lvl_ptr = nullptr;       // per cell nlvl + 1
@@ -33,34 +36,39 @@ struct DevPlan {
   const int32_t* br_len = nullptr;        // [nb]
   const int32_t* br_parent = nullptr;     // [nb]
   const int32_t* child_ptr = nullptr;     // [nb + 1]
-  const int32_t* child = nullptr;         // [nb - n_roots]
-  // warp tasks
+  const int32_t* child = nullptr;         // [nb - roots]
+  // warp tasks over units (whole cells, subtrees, top parts)
   int32_t n_wtasks = 0;
   const int32_t* task_nlvl = nullptr;     // [n_wtasks]
   const int64_t* task_lvl_off = nullptr;  // [n_wtasks]
   const int32_t* tlvl_ptr = nullptr;      // per task nlvl + 1 positions
   const BrMetaT* tmeta = nullptr;         // [nb] by position
-  const int32_t* tchild = nullptr;        // child positions
-  int32_t* counter = nullptr;             // work counter (workspace)
-  int32_t grid_f64 = 1, grid_f32 = 1, grid_cable = 1, grid_comp = 1;  // persistent grid sizes
+  const int32_t* tchild = nullptr;        // child positions (non-contiguous children)
+  const int32_t* phase_entry = nullptr;   // 4 * task + visits, phases A, B, C concatenated
+  int32_t phase_off[4] = {0, 0, 0, 0};
+  int32_t* counter = nullptr;             // [4] work counters (workspace)
+  int32_t grid[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // persistent grid size per kernel kind
   // workspace
-  void* fac = nullptr;    // n_unknowns * 8 bytes: eliminated diagonal (FP64), or two FP32 arrays
-  void* cd = nullptr;     // n_branches * 8 bytes: child-to-parent diagonal contribution
-  void* cb = nullptr;     // n_branches * 8 bytes: child-to-parent right-hand-side contribution
+  void* fac = nullptr;    // n_unknowns * 8 bytes: factor (FP64 / FP32 solves), FP32 working arrays (refine)
+  void* cd = nullptr;     // n_branches * 16 bytes: child-to-parent contribution (or root solution) per position
+  void* cb = nullptr;     // n_branches * 8 bytes: FP32/FP64 per-branch contribution (CTA-per-cell kernels)
+  void* dstate = nullptr; // n_branches * 16 bytes: folded distal state per position (compensated)
+  void* xlast = nullptr;  // n_branches * 8 bytes: solution at the distal compartment per position
   void* red = nullptr;    // n_cells * 8 bytes: per-cell reductions
   int32_t* status = nullptr;  // device status word
 };
 
-// warp-task kernels; prepare_warp_kernels sets their shared-memory limits and
-// persistent grid sizes once per plan (outside any stream capture)
-cudaError_t prepare_warp_kernels(DevPlan& P);
-cudaError_t launch_warp_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s);
-cudaError_t launch_warp_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s);
-cudaError_t launch_warp_solve_compensated(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
+// Warp-task kernels (unit_kernels.cu).  prepare_unit_kernels sets their
+// shared-memory limits and persistent grid sizes once per plan.
+cudaError_t prepare_unit_kernels(DevPlan& P);
+cudaError_t launch_unit_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s);
+cudaError_t launch_unit_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s);
+cudaError_t launch_unit_solve_compensated(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
                                           cudaStream_t s);
-cudaError_t launch_warp_cable(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
+cudaError_t launch_unit_cable(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
                               double dt, double E, int theta, bool rhs_from_V, cudaStream_t s);
 
+// CTA-per-cell kernels (hines_kernels.cu).
 cudaError_t launch_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s);
 cudaError_t launch_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s);
 cudaError_t launch_solve_refine(const DevPlan& P, const float* d, const float* u, const float* b, double* x,

@@ -139,7 +139,7 @@ void cap_branches(std::vector<Br>& bs, int32_t cap) {
 }  // namespace
 
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,
-                    HostPlan& P) {
+                    int sort_by_length, HostPlan& P) {
   if (n_cells < 0 || (n_cells > 0 && !ncomp)) return HINES_ERR_INVALID_ARG;
   P = HostPlan();
   P.n_cells = n_cells;
@@ -246,70 +246,159 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
   std::stable_sort(P.task_cell.begin(), P.task_cell.end(),
                    [&](int32_t x, int32_t y) { return ncomp[x] > ncomp[y]; });
 
-  // warp tasks: next-fit packing of cells in the order above while every
-  // level of the task holds at most kLanes branches (Section 4)
-  std::vector<std::vector<int32_t>> task_cells;
-  std::vector<int32_t> cnt;  // branches per level of the open task
-  std::vector<int32_t> ccnt;
-  for (int32_t c : P.task_cell) {
-    const int64_t lo = P.cell_br_off[(size_t)c], hi = P.cell_br_off[(size_t)c + 1];
-    if (lo == hi) continue;  // empty cell: nothing to solve
-    ccnt.assign((size_t)P.cell_nlvl[(size_t)c], 0);
-    for (int64_t b = lo; b < hi; ++b) ccnt[(size_t)P.br_level[(size_t)b]]++;
-    bool fits = !task_cells.empty();
-    if (fits)
-      for (size_t l = 0; l < ccnt.size(); ++l)
-        if ((l < cnt.size() ? cnt[l] : 0) + ccnt[l] > kLanes) {
-          fits = false;
-          break;
-        }
-    if (!fits) {
-      task_cells.emplace_back();
-      cnt.clear();
-    }
-    task_cells.back().push_back(c);
-    if (cnt.size() < ccnt.size()) cnt.resize(ccnt.size(), 0);
-    for (size_t l = 0; l < ccnt.size(); ++l) cnt[l] += ccnt[l];
+  // units: a cell of at most kUnitMax compartments is one unit; a larger cell
+  // is cut into its top part (the branches whose subtree holds more than
+  // kUnitMax compartments; connected, contains the root) and one subtree unit
+  // per remaining branch whose parent is in the top part
+  std::vector<int64_t> sub((size_t)nb, 0);
+  for (int64_t b = nb - 1; b >= 0; --b) {
+    sub[(size_t)b] += P.br_len[(size_t)b];
+    if (P.br_parent[(size_t)b] >= 0) sub[(size_t)P.br_parent[(size_t)b]] += sub[(size_t)b];
   }
-  // largest task first (ties: order of creation)
-  std::vector<int64_t> tsize(task_cells.size(), 0);
-  for (size_t t = 0; t < task_cells.size(); ++t)
-    for (int32_t c : task_cells[t]) tsize[t] += ncomp[c];
-  std::vector<int32_t> tperm(task_cells.size());
-  std::iota(tperm.begin(), tperm.end(), 0);
-  std::stable_sort(tperm.begin(), tperm.end(), [&](int32_t x, int32_t y) { return tsize[(size_t)x] > tsize[(size_t)y]; });
-  P.n_tasks = (int32_t)task_cells.size();
-  P.cell_task.assign((size_t)n_cells, -1);
-  P.task_nlvl.resize((size_t)P.n_tasks);
-  P.task_lvl_off.resize((size_t)P.n_tasks);
+  struct Unit {
+    int32_t cell, root, kind;
+    int64_t size;
+    int32_t nlvl;
+  };
+  std::vector<Unit> units;
+  std::vector<int32_t> unit_of((size_t)nb, -1);
+  P.br_kind.assign((size_t)nb, 0);
+  for (int32_t c = 0; c < n_cells; ++c) {
+    const int64_t lo = P.cell_br_off[(size_t)c], hi = P.cell_br_off[(size_t)c + 1];
+    if (lo == hi) continue;
+    const bool split = ncomp[c] > kUnitMax;
+    int32_t top_unit = -1;
+    for (int64_t b = lo; b < hi; ++b) {  // parents before children
+      const int32_t pb = P.br_parent[(size_t)b];
+      int32_t u;
+      if (!split) {
+        if (b == lo) units.push_back({c, (int32_t)b, 0, 0, 0});
+        u = (int32_t)units.size() - 1;
+      } else if (sub[(size_t)b] > kUnitMax) {
+        if (top_unit < 0) {
+          units.push_back({c, (int32_t)b, 2, 0, 0});
+          top_unit = (int32_t)units.size() - 1;
+        }
+        u = top_unit;
+      } else if (pb < 0 || P.br_kind[(size_t)pb] == 2) {
+        units.push_back({c, (int32_t)b, 1, 0, 0});
+        u = (int32_t)units.size() - 1;
+      } else {
+        u = unit_of[(size_t)pb];
+      }
+      unit_of[(size_t)b] = u;
+      P.br_kind[(size_t)b] = units[(size_t)u].kind;
+    }
+  }
+  P.br_rlevel.assign((size_t)nb, 0);
+  std::vector<std::vector<int32_t>> unit_br(units.size());
+  for (int64_t b = 0; b < nb; ++b) {
+    const int32_t u = unit_of[(size_t)b];
+    if (u < 0) continue;
+    const int32_t rl = P.br_level[(size_t)b] - P.br_level[(size_t)units[(size_t)u].root];
+    P.br_rlevel[(size_t)b] = rl;
+    units[(size_t)u].size += P.br_len[(size_t)b];
+    units[(size_t)u].nlvl = std::max(units[(size_t)u].nlvl, rl + 1);
+    unit_br[(size_t)u].push_back((int32_t)b);
+  }
+
+  // tasks: per kind, units largest first (ties by cell, then root branch),
+  // packed next-fit while every relative level holds at most kLanes branches
+  // (Section 4's rule with the 32 lanes of a warp)
+  P.n_tasks = 0;
+  P.task_kind.clear();
+  P.task_nlvl.clear();
+  P.task_lvl_off.clear();
+  P.tlvl_ptr.clear();
   P.torder.clear();
   P.torder.reserve((size_t)nb);
-  P.tlvl_ptr.clear();
-  std::vector<int32_t> ids;
-  for (int32_t t = 0; t < P.n_tasks; ++t) {
-    const auto& cs = task_cells[(size_t)tperm[(size_t)t]];
-    int32_t nl = 0;
-    ids.clear();
-    for (int32_t c : cs) {
-      P.cell_task[(size_t)c] = t;
-      nl = std::max(nl, P.cell_nlvl[(size_t)c]);
-      for (int64_t b = P.cell_br_off[(size_t)c]; b < P.cell_br_off[(size_t)c + 1]; ++b) ids.push_back((int32_t)b);
-    }
-    std::stable_sort(ids.begin(), ids.end(), [&](int32_t x, int32_t y) {
-      if (P.br_level[(size_t)x] != P.br_level[(size_t)y]) return P.br_level[(size_t)x] < P.br_level[(size_t)y];
-      if (P.br_len[(size_t)x] != P.br_len[(size_t)y]) return P.br_len[(size_t)x] > P.br_len[(size_t)y];
-      if (P.br_cell[(size_t)x] != P.br_cell[(size_t)y]) return P.br_cell[(size_t)x] < P.br_cell[(size_t)y];
-      return x < y;
+  P.br_task.assign((size_t)nb, -1);
+  std::vector<int64_t> task_size;
+  for (int32_t kind = 0; kind < 3; ++kind) {
+    std::vector<int32_t> us;
+    for (size_t u = 0; u < units.size(); ++u)
+      if (units[u].kind == kind) us.push_back((int32_t)u);
+    std::stable_sort(us.begin(), us.end(), [&](int32_t x, int32_t y) {
+      if (units[(size_t)x].size != units[(size_t)y].size) return units[(size_t)x].size > units[(size_t)y].size;
+      if (units[(size_t)x].cell != units[(size_t)y].cell) return units[(size_t)x].cell < units[(size_t)y].cell;
+      return units[(size_t)x].root < units[(size_t)y].root;
     });
-    P.task_nlvl[(size_t)t] = nl;
-    P.task_lvl_off[(size_t)t] = (int64_t)P.tlvl_ptr.size();
-    const int32_t base = (int32_t)P.torder.size();
-    size_t k = 0;
-    for (int32_t l = 0; l <= nl; ++l) {
-      while (k < ids.size() && P.br_level[(size_t)ids[k]] < l) ++k;
-      P.tlvl_ptr.push_back(base + (int32_t)k);
+    std::vector<std::vector<int32_t>> groups;
+    std::vector<int32_t> cnt, ucnt;
+    for (int32_t u : us) {
+      ucnt.assign((size_t)units[(size_t)u].nlvl, 0);
+      for (int32_t b : unit_br[(size_t)u]) ucnt[(size_t)P.br_rlevel[(size_t)b]]++;
+      bool fits = !groups.empty();
+      if (fits)
+        for (size_t l = 0; l < ucnt.size(); ++l)
+          if ((l < cnt.size() ? cnt[l] : 0) + ucnt[l] > kLanes) {
+            fits = false;
+            break;
+          }
+      if (!fits) {
+        groups.emplace_back();
+        cnt.clear();
+      }
+      groups.back().push_back(u);
+      if (cnt.size() < ucnt.size()) cnt.resize(ucnt.size(), 0);
+      for (size_t l = 0; l < ucnt.size(); ++l) cnt[l] += ucnt[l];
     }
-    P.torder.insert(P.torder.end(), ids.begin(), ids.end());
+    std::vector<int32_t> ids;
+    for (const auto& g : groups) {
+      const int32_t t = P.n_tasks++;
+      int32_t nl = 0;
+      int64_t size = 0;
+      ids.clear();
+      for (int32_t u : g) {
+        nl = std::max(nl, units[(size_t)u].nlvl);
+        size += units[(size_t)u].size;
+        ids.insert(ids.end(), unit_br[(size_t)u].begin(), unit_br[(size_t)u].end());
+      }
+      std::stable_sort(ids.begin(), ids.end(), [&](int32_t x, int32_t y) {
+        if (P.br_rlevel[(size_t)x] != P.br_rlevel[(size_t)y]) return P.br_rlevel[(size_t)x] < P.br_rlevel[(size_t)y];
+        if (sort_by_length && P.br_len[(size_t)x] != P.br_len[(size_t)y])
+          return P.br_len[(size_t)x] > P.br_len[(size_t)y];
+        if (P.br_cell[(size_t)x] != P.br_cell[(size_t)y]) return P.br_cell[(size_t)x] < P.br_cell[(size_t)y];
+        return x < y;
+      });
+      P.task_kind.push_back(kind);
+      P.task_nlvl.push_back(nl);
+      P.task_lvl_off.push_back((int64_t)P.tlvl_ptr.size());
+      const int32_t base = (int32_t)P.torder.size();
+      size_t k = 0;
+      for (int32_t l = 0; l <= nl; ++l) {
+        while (k < ids.size() && P.br_rlevel[(size_t)ids[k]] < l) ++k;
+        P.tlvl_ptr.push_back(base + (int32_t)k);
+      }
+      for (int32_t b : ids) P.br_task[(size_t)b] = t;
+      P.torder.insert(P.torder.end(), ids.begin(), ids.end());
+      task_size.push_back(size);
+    }
+  }
+  // phases: A = whole-cell tasks (both visits) and subtree tasks (elimination),
+  // heaviest first; B = top parts (both visits); C = subtree tasks
+  // (substitution).  Entry = 4 * task + visits (0: both, 1: elimination, 2: substitution).
+  {
+    std::vector<int32_t> a, b, c;
+    for (int32_t t = 0; t < P.n_tasks; ++t) {
+      if (P.task_kind[(size_t)t] == 0) a.push_back(4 * t + 0);
+      if (P.task_kind[(size_t)t] == 1) {
+        a.push_back(4 * t + 1);
+        c.push_back(4 * t + 2);
+      }
+      if (P.task_kind[(size_t)t] == 2) b.push_back(4 * t + 0);
+    }
+    auto work = [&](int32_t e) { return task_size[(size_t)(e >> 2)] * ((e & 3) == 0 ? 2 : 1); };
+    auto heavy_first = [&](std::vector<int32_t>& v) {
+      std::stable_sort(v.begin(), v.end(), [&](int32_t x, int32_t y) { return work(x) > work(y); });
+    };
+    heavy_first(a);
+    heavy_first(b);
+    heavy_first(c);
+    P.phase_off = {0, (int32_t)a.size(), (int32_t)(a.size() + b.size()), (int32_t)(a.size() + b.size() + c.size())};
+    P.phase_entry = a;
+    P.phase_entry.insert(P.phase_entry.end(), b.begin(), b.end());
+    P.phase_entry.insert(P.phase_entry.end(), c.begin(), c.end());
   }
   P.tpos.assign((size_t)nb, -1);
   for (size_t k = 0; k < P.torder.size(); ++k) P.tpos[(size_t)P.torder[k]] = (int32_t)k;

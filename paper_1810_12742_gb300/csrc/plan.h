@@ -27,25 +27,37 @@ struct HostPlan {
   std::vector<int32_t> lvl_ptr;      // per cell nlvl + 1 indices into order
   std::vector<int32_t> task_cell;    // cells in processing order (cost descending)
 
-  // warp tasks (Section 4 packing with 32 lanes): groups of cells processed
-  // by one warp level by level, largest task first
+  // units and warp tasks.  A unit is a whole cell of at most kUnitMax
+  // compartments, or, for a larger cell, its top part (kind 2) or one of the
+  // subtrees hanging below it (kind 1).  Units of one kind are packed into warp
+  // tasks (Section 4's rule with 32 lanes: every level, counted from the
+  // unit's root, holds at most 32 branches), so each level of a task is one
+  // chunk of at most 32 branches, one per lane.
+  std::vector<int32_t> br_kind;      // [nb] kind of the branch's unit (0 whole, 1 subtree, 2 top)
+  std::vector<int32_t> br_rlevel;    // [nb] level relative to the unit's root branch
+  std::vector<int32_t> br_task;      // [nb] task of the branch
   int32_t n_tasks = 0;
-  std::vector<int32_t> cell_task;    // [n_cells] task of each cell
+  std::vector<int32_t> task_kind;    // [n_tasks]
   std::vector<int32_t> task_nlvl;    // [n_tasks]
   std::vector<int64_t> task_lvl_off; // [n_tasks] index of the task's first entry in tlvl_ptr
-  std::vector<int32_t> tlvl_ptr;     // per task nlvl + 1 indices into torder
-  std::vector<int32_t> torder;       // [nb] per task, level ascending, within a level
-                                     // length desc, then cell, then branch id
+  std::vector<int32_t> tlvl_ptr;     // per task nlvl + 1 positions into torder
+  std::vector<int32_t> torder;       // [nb] per task, relative level ascending, within a level
+                                     // cell then branch id (length desc first if sorted)
   std::vector<int32_t> tpos;         // [nb] position of each branch in torder
   std::vector<int32_t> tchild_ptr;   // [nb + 1] children of the branch at each position, CSR
   std::vector<int32_t> tchild;       // child positions (by first compartment descending)
+  // launch phases: entries 4 * task + visits (0 both, 1 elimination, 2 substitution)
+  std::vector<int32_t> phase_off;    // [4]
+  std::vector<int32_t> phase_entry;
 };
 
 constexpr int kLanes = 32;       // branches per chunk (one per lane)
-constexpr int kBranchCap = 32;   // maximum compartments per branch after capping
+constexpr int kBranchCap = 16;   // maximum compartments per branch after capping
+constexpr int kWarpsPerCta = 4;  // warps per CTA of the task kernels (each warp runs its own task)
+constexpr int64_t kUnitMax = 4096;  // largest unit (compartments); larger cells are cut
 
 // Return codes follow hines_status.
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,
-                    HostPlan& out);
+                    int sort_by_length, HostPlan& out);
 
 }  // namespace hines

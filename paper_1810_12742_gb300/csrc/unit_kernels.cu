@@ -1,0 +1,533 @@
+// Warp-task kernels of the batched Hines solver, sm_103a.
+//
+// The planner cuts every cell into units -- whole small cells, or the top part
+// and the subtrees of a large cell -- and packs units into tasks so that every
+// level of a task (counted from its units' roots) holds at most 32 branches
+// (Section 4's rule with the 32 lanes of a warp).  A warp owns a task and walks
+// its levels, one level = one chunk of at most 32 branches, one per lane:
+// deepest level first for the elimination, root level first for the
+// substitution (Section 3).  Inside a branch the parent of compartment i is
+// i - 1 (Section 5): each lane runs a Thomas chain (Listing 1) and leaves one
+// contribution for its parent compartment (Listing 2's parent lookup).
+//
+// A solve is three launches: (A) whole-cell tasks (both sweeps) and the
+// elimination of subtree tasks; (B) top parts (both sweeps); (C) the
+// substitution of subtree tasks.  Within a launch no warp waits for another.
+//
+// The levels of a task follow one another in the same warp, so a chunk's
+// children are the lanes of the chunk just before it (elimination) and its
+// parents likewise (substitution): those values pass through a small shared
+// memory cache; only values crossing task boundaries go through global
+// memory.  The next chunk's inputs are staged with cp.async into a second
+// buffer while the current one is computed, in an interleaved layout
+// (Section 5) whose column is XOR-swizzled by the row so that the warp's
+// copies and the lanes' chain steps are free of bank conflicts.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/hines.h"
+#include "device_common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+namespace hines {
+namespace {
+
+using namespace dev;
+
+constexpr int kL = kBranchCap;      // compartments per branch, at most
+constexpr int kSlots = 32 * kL;     // one staged array of one chunk
+constexpr int kWarps = kWarpsPerCta;
+
+struct Meta {
+  long long first, pcomp;
+  int ppos, cpos, len, nchild, ccontig;
+  float4 ds;  // compensated substitution: folded distal state left by the elimination
+};
+
+__device__ __forceinline__ Meta load_meta(const DevPlan& P, int pos, bool valid, bool want_ds) {
+  Meta m{0, -1, -1, 0, 0, 0, 0, make_float4(0.f, 0.f, 0.f, 0.f)};
+  if (valid) {
+    if (want_ds) m.ds = static_cast<const float4*>(P.dstate)[pos];
+    const BrMetaT t = P.tmeta[pos];
+    m.first = t.first;
+    m.pcomp = t.pcomp;
+    m.ppos = t.ppos;
+    m.cpos = t.cpos;
+    m.len = t.len;
+    m.nchild = t.nchild;
+    m.ccontig = t.ccontig;
+  }
+  return m;
+}
+
+__device__ __forceinline__ int child_pos(const DevPlan& P, const Meta& m, int i) {
+  return m.ccontig ? m.cpos + i : __ldg(P.tchild + m.cpos + i);
+}
+
+// The chunk processed just before the current one in the same sweep.
+struct Prev {
+  int c0, n, which;  // n = 0: none
+};
+
+// Per-branch copy of up to two branches per step (branches are at most 16 long).
+template <typename T, typename F>
+__device__ __forceinline__ void for_branch_elements(const Meta& m, int n, int lane, F&& f) {
+  const int half = lane >> 4, t = lane & 15;
+  for (int j = 0; j < n; j += 2) {
+    const int jj = j + half;
+    const long long fj = __shfl_sync(kFull, m.first, jj & 31);
+    const int lj = __shfl_sync(kFull, m.len, jj & 31);
+    const long long pc = __shfl_sync(kFull, m.pcomp, jj & 31);
+    if (jj < n && t < lj) f(jj, t, lj, fj, pc);
+  }
+}
+
+// ============================================================================
+// Compensated mode: FP32 inputs, double-float arithmetic from FP32 error-free
+// transformations, FP64 solution.  The elimination keeps nothing per
+// compartment: it leaves, per branch, its contribution to the parent (or the
+// root's solution) and its folded distal state; the substitution re-stages the
+// chunk and re-eliminates it from that state before substituting.
+// ============================================================================
+struct CompMode {
+  struct Args {
+    const float* d;
+    const float* u;
+    const float* b;
+    double* x;
+  };
+  static constexpr int kStageBytes = 3 * kSlots * 4;
+  static constexpr int kCacheBytes = 2 * 32 * 16 + 2 * 32 * 8;
+  static constexpr int kWarpBytes = 2 * kStageBytes + kCacheBytes;
+
+  static constexpr bool kWantDs = true;
+
+  __device__ static void stage(const DevPlan&, const Args& A, int, const Meta& m, int n, int lane,
+                               unsigned char* buf) {
+    float* sd = reinterpret_cast<float*>(buf);
+    float* su = sd + kSlots;
+    float* sb = su + kSlots;
+    for_branch_elements<float>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+      const int q = sidx(lj - 1 - t, jj);
+      cp_async4(&sd[q], A.d + fj + t);
+      cp_async4(&su[q], A.u + fj + t);
+      cp_async4(&sb[q], A.b + fj + t);
+    });
+    cp_commit();
+  }
+
+  __device__ static void compute(const DevPlan& P, const Args&, int visit, int c0, int n, int lane, const Meta& m,
+                                 unsigned char* buf, const Prev& pv, unsigned char* cache, int cur) {
+    float* sd = reinterpret_cast<float*>(buf);
+    const float* su = sd + kSlots;
+    float* sb = sd + 2 * kSlots;
+    float4* cslot = reinterpret_cast<float4*>(cache);        // [2][32] contributions
+    float2* cx = reinterpret_cast<float2*>(cache + 2 * 32 * 16);  // [2][32] distal solutions
+    float4* slot = static_cast<float4*>(P.cd);
+    float4* dst = static_cast<float4*>(P.dstate);
+    float2* xlast = static_cast<float2*>(P.xlast);
+    if (lane >= n) return;
+    const int pos = c0 + lane;
+    const int len = m.len;
+    if (visit == 0) {
+      ff Dv = {sd[sidx(0, lane)], 0.f}, Bv = {sb[sidx(0, lane)], 0.f};
+      for (int i = 0; i < m.nchild; ++i) {
+        const int cp = child_pos(P, m, i);
+        const int loc = cp - pv.c0;
+        const float4 v = (loc >= 0 && loc < pv.n) ? cslot[pv.which * 32 + loc] : slot[cp];
+        Dv = ff_sub(Dv, v.x, v.y);
+        Bv = ff_sub(Bv, v.z, v.w);
+      }
+      dst[pos] = make_float4(Dv.h, Dv.l, Bv.h, Bv.l);
+      for (int k = 0; k < len - 1; ++k) {
+        const float uk = su[sidx(k, lane)];
+        const ff f = ff_div_f(uk, Dv);
+        const ff fu = ff_mul_f(f, uk);
+        const ff fb = ff_mul(f, Bv);
+        Dv = ff_sub_dom(sd[sidx(k + 1, lane)], fu.h, fu.l);
+        Bv = ff_sub({sb[sidx(k + 1, lane)], 0.f}, fb.h, fb.l);
+      }
+      float4 out;
+      if (m.pcomp >= 0) {
+        const float uk = su[sidx(len - 1, lane)];
+        const ff f = ff_div_f(uk, Dv);
+        const ff fu = ff_mul_f(f, uk);
+        const ff fb = ff_mul(f, Bv);
+        out = make_float4(fu.h, fu.l, fb.h, fb.l);
+      } else {
+        const ff x0 = ff_div(Bv, Dv);  // solve root
+        out = make_float4(x0.h, x0.l, 0.f, 0.f);
+      }
+      slot[pos] = out;
+      cslot[cur * 32 + lane] = out;
+      return;
+    }
+    ff Dv = {m.ds.x, m.ds.y}, Bv = {m.ds.z, m.ds.w};
+    float el[kL], bl[kL];
+#pragma unroll
+    for (int k = 0; k < kL; ++k) {
+      if (k < len) {
+        const int q = sidx(k, lane);
+        sd[q] = Dv.h;
+        el[k] = Dv.l;
+        sb[q] = Bv.h;
+        bl[k] = Bv.l;
+        if (k < len - 1) {
+          const float uk = su[q];
+          const ff f = ff_div_f(uk, Dv);
+          const ff fu = ff_mul_f(f, uk);
+          const ff fb = ff_mul(f, Bv);
+          const int q1 = sidx(k + 1, lane);
+          Dv = ff_sub_dom(sd[q1], fu.h, fu.l);
+          Bv = ff_sub({sb[q1], 0.f}, fb.h, fb.l);
+        }
+      }
+    }
+    ff xp = {0.f, 0.f};
+    if (m.pcomp >= 0) {
+      const int loc = m.ppos - pv.c0;
+      const float2 t = (loc >= 0 && loc < pv.n) ? cx[pv.which * 32 + loc] : xlast[m.ppos];
+      xp = {t.x, t.y};
+    }
+#pragma unroll
+    for (int k = kL - 1; k >= 0; --k) {
+      if (k < len) {
+        const int q = sidx(k, lane);
+        ff xi;
+        if (m.pcomp < 0 && k == len - 1) {
+          const float4 t = slot[pos];
+          xi = {t.x, t.y};
+        } else {
+          const float uk = su[q];
+          const float M = __fmul_rn(uk, xp.h);
+          float mm = fmaf(uk, xp.h, -M);
+          mm = fmaf(uk, xp.l, mm);
+          const ff num = ff_sub({sb[q], bl[k]}, M, mm);
+          xi = ff_div(num, {sd[q], el[k]});
+        }
+        const double xd = ff_to_double(xi.h, xi.l);
+        sd[q] = __int_as_float(__double2loint(xd));
+        sb[q] = __int_as_float(__double2hiint(xd));
+        xp = xi;
+      }
+    }
+    const float2 xo = make_float2(xp.h, xp.l);
+    xlast[pos] = xo;
+    cx[cur * 32 + lane] = xo;
+  }
+
+  __device__ static void copy_out(const DevPlan&, const Args& A, int visit, const Meta& m, int n, int lane,
+                                  unsigned char* buf) {
+    if (visit == 0) return;
+    const float* sd = reinterpret_cast<const float*>(buf);
+    const float* sb = sd + 2 * kSlots;
+    for_branch_elements<float>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+      const int q = sidx(lj - 1 - t, jj);
+      A.x[fj + t] = __hiloint2double(__float_as_int(sb[q]), __float_as_int(sd[q]));
+    });
+  }
+};
+
+// ============================================================================
+// Factor mode (FP64, FP32, passive cable): the elimination writes the
+// reciprocal eliminated diagonal to the workspace and the eliminated
+// right-hand side in place; the substitution reads them back.  In cable mode
+// the system is rebuilt while staging (Section 1's implicit-Euler system):
+// d_i = s_i (1 + theta dt g_i) + sum of a over the edges at i (a = -u),
+// b_i = s_i V_i + s_i dt g_i (E - (1 - theta) V_i).
+// ============================================================================
+template <typename T, bool kCable>
+struct FactorMode {
+  struct Args {
+    const T* d;
+    const T* u;
+    const T* s;  // cable: s, g
+    const T* g;
+    T* x;        // right-hand side in, solution out (cable: V in, V out)
+    T dt, E, theta;
+    bool rhs_from_V;
+  };
+  static constexpr int kStageBytes = 3 * kSlots * (int)sizeof(T);
+  static constexpr int kCacheBytes = 2 * 32 * 2 * (int)sizeof(T) + 2 * 32 * (int)sizeof(T);
+  static constexpr int kWarpBytes = 2 * kStageBytes + kCacheBytes;
+
+  static constexpr bool kWantDs = false;
+
+  __device__ static void stage(const DevPlan& P, const Args& A, int visit, const Meta& m, int n, int lane,
+                               unsigned char* buf) {
+    T* sd = reinterpret_cast<T*>(buf);
+    T* su = sd + kSlots;
+    T* sb = su + kSlots;
+    if (visit == 1) {
+      const T* fac = static_cast<const T*>(P.fac);
+      for_branch_elements<T>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+        const int q = sidx(lj - 1 - t, jj);
+        cp_async(&sd[q], fac + fj + t);
+        cp_async(&su[q], A.u + fj + t);
+        cp_async(&sb[q], A.x + fj + t);
+      });
+    } else if (!kCable) {
+      for_branch_elements<T>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+        const int q = sidx(lj - 1 - t, jj);
+        cp_async(&sd[q], A.d + fj + t);
+        cp_async(&su[q], A.u + fj + t);
+        cp_async(&sb[q], A.x + fj + t);
+      });
+    } else {
+      for_branch_elements<T>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long pc) {
+        const long long i = fj + t;
+        const T si = A.s[i], gi = A.g[i], ui = A.u[i], vi = A.x[i];
+        T dd = si * (T(1) + A.theta * A.dt * gi);
+        if (!(pc < 0 && t == 0)) dd -= ui;  // own edge to the parent
+        const T bb = A.rhs_from_V ? si * vi + si * A.dt * gi * (A.E - (T(1) - A.theta) * vi) : vi;
+        const int q = sidx(lj - 1 - t, jj);
+        sd[q] = dd;
+        su[q] = ui;
+        sb[q] = bb;
+      });
+    }
+    cp_commit();
+  }
+
+  __device__ static void compute(const DevPlan& P, const Args& A, int visit, int c0, int n, int lane, const Meta& m,
+                                 unsigned char* buf, const Prev& pv, unsigned char* cache, int cur) {
+    T* sd = reinterpret_cast<T*>(buf);
+    const T* su = sd + kSlots;
+    T* sb = sd + 2 * kSlots;
+    T* cslot = reinterpret_cast<T*>(cache);                   // [2][32][2] contributions
+    T* cx = cslot + 2 * 32 * 2;                               // [2][32] distal solutions
+    T* slot = static_cast<T*>(P.cd);                          // [nb][2]
+    if (lane >= n) return;
+    const int pos = c0 + lane;
+    const int len = m.len;
+    if (visit == 0) {
+      T D = sd[sidx(0, lane)], B = sb[sidx(0, lane)];
+      for (int i = 0; i < m.nchild; ++i) {
+        const int cp = child_pos(P, m, i);
+        const int loc = cp - pv.c0;
+        const bool local = loc >= 0 && loc < pv.n;
+        D -= local ? cslot[(pv.which * 32 + loc) * 2] : slot[2 * cp];
+        B -= local ? cslot[(pv.which * 32 + loc) * 2 + 1] : slot[2 * cp + 1];
+      }
+      for (int k = 0; k < len - 1; ++k) {
+        const T uk = su[sidx(k, lane)];
+        const T r = rcp_t(D);
+        sd[sidx(k, lane)] = r;
+        sb[sidx(k, lane)] = B;
+        const T f = uk * r;
+        D = sd[sidx(k + 1, lane)] - f * uk;
+        if (kCable) D -= uk;  // the edge to the chain child
+        B = sb[sidx(k + 1, lane)] - f * B;
+      }
+      const int k = len - 1;
+      const T r = rcp_t(D);
+      sd[sidx(k, lane)] = r;
+      T c0v = T(0), c1v = T(0);
+      if (m.pcomp >= 0) {
+        sb[sidx(k, lane)] = B;
+        const T uk = su[sidx(k, lane)];
+        const T f = uk * r;
+        c0v = kCable ? f * uk + uk : f * uk;
+        c1v = f * B;
+      } else {
+        sb[sidx(k, lane)] = B * r;  // solve root
+      }
+      slot[2 * pos] = c0v;
+      slot[2 * pos + 1] = c1v;
+      cslot[(cur * 32 + lane) * 2] = c0v;
+      cslot[(cur * 32 + lane) * 2 + 1] = c1v;
+      return;
+    }
+    T xp = T(0);
+    if (m.pcomp >= 0) {
+      const int loc = m.ppos - pv.c0;
+      xp = (loc >= 0 && loc < pv.n) ? cx[pv.which * 32 + loc] : A.x[m.pcomp];
+    }
+    for (int k = len - 1; k >= 0; --k) {
+      const int q = sidx(k, lane);
+      const T xi = (m.pcomp < 0 && k == len - 1) ? sb[q] : (sb[q] - su[q] * xp) * sd[q];
+      sb[q] = xi;
+      xp = xi;
+    }
+    cx[cur * 32 + lane] = xp;
+  }
+
+  __device__ static void copy_out(const DevPlan& P, const Args& A, int visit, const Meta& m, int n, int lane,
+                                  unsigned char* buf) {
+    const T* sd = reinterpret_cast<const T*>(buf);
+    const T* sb = sd + 2 * kSlots;
+    T* fac = static_cast<T*>(P.fac);
+    for_branch_elements<T>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+      const int q = sidx(lj - 1 - t, jj);
+      if (visit == 0) fac[fj + t] = sd[q];
+      A.x[fj + t] = sb[q];
+    });
+  }
+};
+
+// ============================================================================
+// Task driver
+// ============================================================================
+// Position in a task's chunk sequence: levels deepest-first for the
+// elimination (visit 0), root-first for the substitution (visit 1); a level of
+// more than 32 branches is several chunks.
+struct Pos {
+  int visit, l, c0, n;  // visit == ve: past the end
+};
+
+__device__ __forceinline__ Pos pos_level(int visit, int l, const int32_t* lp) {
+  const int c0 = __ldg(lp + l), e = __ldg(lp + l + 1) - c0;
+  return {visit, l, c0, e < 32 ? e : 32};
+}
+
+__device__ __forceinline__ Pos pos_next(Pos p, const int32_t* lp, int nl, int ve) {
+  const int end = __ldg(lp + p.l + 1);
+  if (p.c0 + 32 < end) {
+    p.c0 += 32;
+    p.n = end - p.c0 < 32 ? end - p.c0 : 32;
+    return p;
+  }
+  if (p.visit == 0) {
+    if (p.l > 0) return pos_level(0, p.l - 1, lp);
+    if (ve == 1) return {ve, 0, 0, 0};
+    return pos_level(1, 0, lp);
+  }
+  if (p.l + 1 < nl) return pos_level(1, p.l + 1, lp);
+  return {ve, 0, 0, 0};
+}
+
+template <class M>
+__device__ void run_task(const DevPlan& P, const typename M::Args& A, int t, int code, int lane, unsigned char* wbase) {
+  const int nl = P.task_nlvl[t];
+  const int32_t* lp = P.tlvl_ptr + P.task_lvl_off[t];
+  const int vb = code == 2 ? 1 : 0, ve = code == 1 ? 1 : 2;
+  unsigned char* cache = wbase + 2 * M::kStageBytes;
+  auto buf = [wbase](int which) { return wbase + which * M::kStageBytes; };
+  auto meta = [&](const Pos& p) {
+    return load_meta(P, p.c0 + lane, p.visit < ve && lane < p.n, M::kWantDs && p.visit == 1);
+  };
+  Pos cur = pos_level(vb, vb == 0 ? nl - 1 : 0, lp);
+  Meta m_cur = meta(cur);
+  M::stage(P, A, cur.visit, m_cur, cur.n, lane, buf(0));
+  Pos nxt = pos_next(cur, lp, nl, ve);
+  Meta m_nxt = meta(nxt);
+  Prev pv{0, 0, 0};  // last chunk of the previous level in this sweep
+  int which = 0;
+  while (cur.visit < ve) {
+    cp_wait_all();
+    __syncwarp();
+    // nothing of the substitution is read before the elimination has finished:
+    // its first chunks reuse positions the elimination is still writing
+    const bool crossing = nxt.visit != cur.visit;
+    if (nxt.visit < ve && !crossing) M::stage(P, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1));
+    const Pos nn = nxt.visit < ve ? pos_next(nxt, lp, nl, ve) : nxt;
+    Meta m_nn = meta(nn);
+    M::compute(P, A, cur.visit, cur.c0, cur.n, lane, m_cur, buf(which), pv, cache, cur.l & 1);
+    __syncwarp();
+    M::copy_out(P, A, cur.visit, m_cur, cur.n, lane, buf(which));
+    __syncwarp();
+    if (crossing && nxt.visit < ve) {
+      m_nxt = meta(nxt);
+      m_nn = meta(nn);
+      M::stage(P, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1));
+    }
+    // predecessor of the next chunk: the last chunk of the level before its level, same sweep
+    if (crossing) {
+      pv = Prev{0, 0, 0};
+    } else if (nxt.l != cur.l) {
+      pv = Prev{cur.c0, cur.n, cur.l & 1};
+    }
+    cur = nxt;
+    m_cur = m_nxt;
+    nxt = nn;
+    m_nxt = m_nn;
+    which ^= 1;
+  }
+}
+
+template <class M>
+__global__ void __launch_bounds__(32 * kWarps) k_units(DevPlan P, typename M::Args A, int phase) {
+  extern __shared__ __align__(16) unsigned char smem_u[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* wbase = smem_u + w * M::kWarpBytes;
+  const int e0 = P.phase_off[phase], ne = P.phase_off[phase + 1] - e0;
+  for (;;) {
+    int k = 0;
+    if (lane == 0) k = atomicAdd(P.counter + phase, 1);
+    k = __shfl_sync(kFull, k, 0);
+    if (k >= ne) break;
+    const int e = P.phase_entry[e0 + k];
+    run_task<M>(P, A, e >> 2, e & 3, lane, wbase);
+  }
+}
+
+template <class M>
+cudaError_t grid_of(const DevPlan& P, int* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  const size_t smem = (size_t)kWarps * M::kWarpBytes;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_units<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_units<M>, 32 * kWarps, smem);
+  if (e != cudaSuccess) return e;
+  *grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  return cudaSuccess;
+}
+
+template <class M>
+cudaError_t launch_phases(const DevPlan& P, const typename M::Args& A, int grid, cudaStream_t s) {
+  if (P.n_wtasks == 0) return cudaSuccess;
+  const size_t smem = (size_t)kWarps * M::kWarpBytes;
+  cudaError_t e = cudaMemsetAsync(P.counter, 0, 4 * sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  for (int phase = 0; phase < 3; ++phase) {
+    const int ne = P.phase_off[phase + 1] - P.phase_off[phase];
+    if (ne == 0) continue;
+    const int warps = ne < grid * kWarps ? ne : grid * kWarps;
+    const int blocks = (warps + kWarps - 1) / kWarps;
+    k_units<M><<<blocks, 32 * kWarps, smem, s>>>(P, A, phase);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+using F64 = FactorMode<double, false>;
+using F32 = FactorMode<float, false>;
+using Cable = FactorMode<double, true>;
+
+}  // namespace
+
+cudaError_t prepare_unit_kernels(DevPlan& P) {
+  cudaError_t e = grid_of<F64>(P, &P.grid[0]);
+  if (e == cudaSuccess) e = grid_of<F32>(P, &P.grid[1]);
+  if (e == cudaSuccess) e = grid_of<Cable>(P, &P.grid[2]);
+  if (e == cudaSuccess) e = grid_of<CompMode>(P, &P.grid[3]);
+  return e;
+}
+
+cudaError_t launch_unit_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s) {
+  F64::Args A{d, u, nullptr, nullptr, b, 0.0, 0.0, 0.0, false};
+  return launch_phases<F64>(P, A, P.grid[0], s);
+}
+
+cudaError_t launch_unit_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s) {
+  F32::Args A{d, u, nullptr, nullptr, b, 0.f, 0.f, 0.f, false};
+  return launch_phases<F32>(P, A, P.grid[1], s);
+}
+
+cudaError_t launch_unit_cable(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
+                              double dt, double E, int theta, bool rhs_from_V, cudaStream_t s) {
+  Cable::Args A{nullptr, u, sv, g, V, dt, E, (double)theta, rhs_from_V};
+  return launch_phases<Cable>(P, A, P.grid[2], s);
+}
+
+cudaError_t launch_unit_solve_compensated(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
+                                          cudaStream_t s) {
+  CompMode::Args A{d, u, b, x};
+  return launch_phases<CompMode>(P, A, P.grid[3], s);
+}
+
+}  // namespace hines

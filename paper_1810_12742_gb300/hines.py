@@ -46,7 +46,7 @@ class HinesError(RuntimeError):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("host_only", ctypes.c_int32), ("split_branches", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("sort_by_length", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -70,7 +70,7 @@ def lib():
             L.hines_plan_layout.argtypes = [vp, vp]
             L.hines_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
             L.hines_plan_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
-            L.hines_plan_export_tasks.argtypes = [vp, vp, vp]
+            L.hines_plan_export_tasks.argtypes = [vp, vp, vp, vp]
             L.hines_solve.argtypes = [vp, i32, vp, vp, vp, vp]
             L.hines_solve_refine.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
             L.hines_solve_compensated.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -111,11 +111,12 @@ class Plan:
     p[0] = -1, p[i] < i), concatenated.  host_only builds the schedule without
     touching the GPU (for inspection)."""
 
-    def __init__(self, ncomp, parent, split_branches: bool = False, host_only: bool = False, cta_threads: int = 0):
+    def __init__(self, ncomp, parent, split_branches: bool = False, host_only: bool = False, cta_threads: int = 0,
+                 sort_by_length: bool = False):
         self._h = ctypes.c_void_p()
         nc = np.ascontiguousarray(ncomp, np.int32)
         pa = np.ascontiguousarray(parent, np.int32)
-        opts = PlanOpts(int(host_only), int(split_branches), int(cta_threads))
+        opts = PlanOpts(int(host_only), int(split_branches), int(cta_threads), int(sort_by_length))
         _check(lib().hines_plan_create(ctypes.byref(self._h), nc.size, _np_ptr(nc), _np_ptr(pa), ctypes.byref(opts)),
                "hines_plan_create")
         info = PlanInfo()
@@ -145,11 +146,10 @@ class Plan:
         return out
 
     def export_tasks(self) -> dict:
-        cell_task = np.empty(self.n_cells, np.int64)
-        task_order = np.empty(self.n_branches, np.int64)
-        _check(lib().hines_plan_export_tasks(self._h, _np_ptr(cell_task), _np_ptr(task_order)),
-               "hines_plan_export_tasks")
-        return {"cell_task": cell_task, "task_order": task_order}
+        out = {k: np.empty(self.n_branches, np.int64) for k in ("branch_task", "branch_kind", "task_order")}
+        _check(lib().hines_plan_export_tasks(self._h, _np_ptr(out["branch_task"]), _np_ptr(out["branch_kind"]),
+                                             _np_ptr(out["task_order"])), "hines_plan_export_tasks")
+        return out
 
     def status(self) -> int:
         st = ctypes.c_int32(0)

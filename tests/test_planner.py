@@ -60,7 +60,7 @@ def py_split(cells):
         level += 1
 
 
-CAP, LANES = 32, 32
+CAP, LANES = 16, 32
 
 
 def py_cap(bs, cap=CAP):
@@ -81,28 +81,73 @@ def py_cap(bs, cap=CAP):
     return out
 
 
-def py_tasks(ncomp, cells, level, length):
-    """Next-fit packing of cells (largest first, ties by index) while every
-    level of a task holds at most 32 branches; tasks largest first; branches
-    of a task by level, length desc, cell, id."""
-    order = sorted(range(len(ncomp)), key=lambda c: (-ncomp[c], c))
-    tasks, cnt = [], []
-    for c in order:
-        if not cells[c]:
+UNIT_MAX = 4096
+
+
+def py_units(ncomp, cells_flat):
+    """Units: a cell of at most UNIT_MAX compartments; or the top part of a
+    larger cell (branches whose subtree holds more than UNIT_MAX compartments)
+    and one unit per remaining branch whose parent is in the top part.
+    cells_flat: list per cell of global branch ids with (len, parent, level)."""
+    units = []  # [kind, cell, root, [ids]]
+    for c, ids in enumerate(cells_flat):
+        if not ids:
             continue
-        cc = np.bincount([b[3] for b in cells[c]])
-        fits = bool(tasks) and all((cnt[l] if l < len(cnt) else 0) + cc[l] <= LANES for l in range(len(cc)))
-        if not fits:
-            tasks.append([])
-            cnt = []
-        tasks[-1].append(c)
-        cnt = [(cnt[l] if l < len(cnt) else 0) + (cc[l] if l < len(cc) else 0) for l in range(max(len(cnt), len(cc)))]
-    sizes = [sum(ncomp[c] for c in t) for t in tasks]
-    perm = sorted(range(len(tasks)), key=lambda t: (-sizes[t], t))
-    return [tasks[t] for t in perm]
+        if ncomp[c] <= UNIT_MAX:
+            units.append([0, c, ids[0], list(ids)])
+            continue
+        sub = {}
+        for b in reversed(ids):
+            sub[b] = sub.get(b, 0) + G["len"][b]
+            pb = G["parent"][b]
+            if pb >= 0:
+                sub[pb] = sub.get(pb, 0) + sub[b]
+        top = [b for b in ids if sub[b] > UNIT_MAX]
+        topset = set(top)
+        units.append([2, c, top[0], top])
+        owner = {}
+        for b in ids:
+            if b in topset:
+                continue
+            pb = G["parent"][b]
+            if pb in topset:
+                units.append([1, c, b, [b]])
+                owner[b] = len(units) - 1
+            else:
+                owner[b] = owner[pb]
+                units[owner[b]][3].append(b)
+    return units
 
 
-def py_plan(ncomp, parent, split=False):
+def py_tasks(ncomp, units, sort_by_length):
+    rl = {}
+    for kind, c, root, ids in units:
+        for b in ids:
+            rl[b] = G["level"][b] - G["level"][root]
+    tasks = []
+    for kind in (0, 1, 2):
+        us = [u for u in units if u[0] == kind]
+        us.sort(key=lambda u: (-sum(G["len"][b] for b in u[3]), u[1], u[2]))
+        groups, cnt = [], []
+        for u in us:
+            cc = np.bincount([rl[b] for b in u[3]])
+            fits = bool(groups) and all((cnt[l] if l < len(cnt) else 0) + cc[l] <= LANES for l in range(len(cc)))
+            if not fits:
+                groups.append([])
+                cnt = []
+            groups[-1].append(u)
+            cnt = [(cnt[l] if l < len(cnt) else 0) + (cc[l] if l < len(cc) else 0) for l in range(max(len(cnt), len(cc)))]
+        for g in groups:
+            ids = [b for u in g for b in u[3]]
+            ids.sort(key=lambda b: (rl[b], -G["len"][b] if sort_by_length else 0, G["cell"][b], b))
+            tasks.append((kind, ids))
+    return tasks
+
+
+G = {}
+
+
+def py_plan(ncomp, parent, split=False, sort_by_length=False):
     off = np.concatenate(([0], np.cumsum(ncomp))).astype(np.int64)
     cells = [py_branches(parent[off[c]:off[c + 1]]) for c in range(len(ncomp))]
     if split:
@@ -123,28 +168,33 @@ def py_plan(ncomp, parent, split=False):
         base += len(bs)
     out = {k: np.array(v, np.int64) for k, v in
            dict(first=first, len=length, parent_branch=pbr, level=level, cell=cell, order=order).items()}
-    tasks = py_tasks(list(ncomp), cells, level, length)
-    cell_task = np.full(len(ncomp), -1, np.int64)
+    G.clear()
+    G.update(len=length, parent=pbr, level=level, cell=cell)
     base_of = np.concatenate(([0], np.cumsum([len(bs) for bs in cells]))).astype(np.int64)
+    cells_flat = [list(range(base_of[c], base_of[c + 1])) for c in range(len(cells))]
+    units = py_units(list(ncomp), cells_flat)
+    tasks = py_tasks(list(ncomp), units, sort_by_length)
+    nb = len(first)
+    branch_task = np.full(nb, -1, np.int64)
+    branch_kind = np.zeros(nb, np.int64)
+    for kind, c, root, ids in units:
+        branch_kind[ids] = kind
     torder = []
-    for t, cs in enumerate(tasks):
-        ids = []
-        for c in cs:
-            cell_task[c] = t
-            ids += list(range(base_of[c], base_of[c + 1]))
-        ids.sort(key=lambda g: (level[g], -length[g], cell[g], g))
+    for t, (kind, ids) in enumerate(tasks):
+        branch_task[ids] = t
         torder += ids
-    out["cell_task"] = cell_task
+    out["branch_task"] = branch_task
+    out["branch_kind"] = branch_kind
     out["task_order"] = np.array(torder, np.int64)
     out["n_tasks"] = len(tasks)
     return out
 
 
-def _compare(ncomp, parent, split):
-    plan = H.Plan(ncomp, parent, split_branches=split, host_only=True)
+def _compare(ncomp, parent, split, sort_by_length=False):
+    plan = H.Plan(ncomp, parent, split_branches=split, host_only=True, sort_by_length=sort_by_length)
     got = plan.export()
     got.update(plan.export_tasks())
-    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split)
+    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split, sort_by_length)
     assert plan.n_tasks == ref.pop("n_tasks")
     for k in ref:
         assert np.array_equal(got[k], ref[k]), k
@@ -154,13 +204,14 @@ def _compare(ncomp, parent, split):
 
 
 @pytest.mark.parametrize("split", [False, True])
-def test_zoo_matches_restatement(split):
+@pytest.mark.parametrize("sort_by_length", [False, True])
+def test_zoo_matches_restatement(split, sort_by_length):
     rng = np.random.default_rng(21)
     trees = []
     for n in (1, 2, 5, 33, 250):
         trees += list(tree_zoo(rng, n).values())
     ncomp = [t.size for t in trees]
-    _compare(ncomp, np.concatenate(trees), split)
+    _compare(ncomp, np.concatenate(trees), split, sort_by_length)
 
 
 @pytest.mark.parametrize("name", ["fp64_small", "fp64_uniform", "uneven_steps", "adjoint"])
@@ -218,7 +269,7 @@ def test_split_shortens_long_branches():
     assert b.max_levels > a.max_levels
 
 
-def test_tasks_respect_lane_rule_and_cover_cells():
+def test_tasks_respect_lane_rule_and_cover_branches():
     w = I.WORKLOADS["uneven_steps"]
     cls = I.cell_classes(w)
     cells = np.concatenate([np.nonzero(cls == 0)[0][:40], np.nonzero(cls == 1)[0][:2]])
@@ -226,13 +277,25 @@ def test_tasks_respect_lane_rule_and_cover_cells():
     plan = H.Plan(ncomp, parent, host_only=True)
     e = plan.export()
     t = plan.export_tasks()
-    assert (t["cell_task"] >= 0).all() and plan.n_tasks < len(cells)
+    assert (t["branch_task"] >= 0).all()
     assert sorted(t["task_order"].tolist()) == list(range(plan.n_branches))
+    # large cells are cut: top parts and subtrees; no subtree unit exceeds 4096 compartments
+    assert set(np.unique(t["branch_kind"]).tolist()) == {0, 1, 2}
+    # every task level (relative to unit roots) holds at most 32 branches
+    pb = e["parent_branch"]
+    kind = t["branch_kind"]
+    root = np.arange(pb.size)
+    for b in range(pb.size):  # unit root: climb while the parent is in the same unit
+        r = b
+        while pb[r] >= 0 and (kind[b] != 1 or kind[pb[r]] == 1):
+            r = pb[r]
+        root[b] = r
+    rl = e["level"] - e["level"][root]
     for task in range(plan.n_tasks):
-        members = np.nonzero(t["cell_task"] == task)[0]
-        lv = e["level"][np.isin(e["cell"], members)]
-        if len(members) > 1:
-            assert np.bincount(lv).max() <= 32
+        sel = t["branch_task"] == task
+        levels = np.bincount(rl[sel])
+        units = len(np.unique(root[sel]))
+        assert units == 1 or levels.max() <= 32  # packing never makes a level wider than 32
 
 
 def test_planner_time_is_linear():
