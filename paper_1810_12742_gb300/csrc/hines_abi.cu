@@ -152,15 +152,17 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
   hines_plan_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 3; ++k)
     if (o.reserved[k] != 0) return HINES_ERR_INVALID_ARG;
+  if (o.pack_compartments < -1) return HINES_ERR_INVALID_ARG;
   if (o.cta_threads == 0) o.cta_threads = 256;
   if (o.cta_threads < 32 || o.cta_threads > 1024 || (o.cta_threads % 32) != 0) return HINES_ERR_INVALID_ARG;
   hines_plan_t p = new (std::nothrow) hines_plan_s();
   if (!p) return HINES_ERR_OOM;
   int rc;
   try {
-    rc = hines::build_host_plan(n_cells, ncomp, parent, o.split_branches, o.sort_by_length, p->host);
+    rc = hines::build_host_plan(n_cells, ncomp, parent, o.split_branches, o.sort_by_length, o.pack_compartments,
+                                p->host);
   } catch (const std::bad_alloc&) {
     rc = HINES_ERR_OOM;
   }

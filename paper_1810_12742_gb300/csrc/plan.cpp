@@ -139,7 +139,7 @@ void cap_branches(std::vector<Br>& bs, int32_t cap) {
 }  // namespace
 
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,
-                    int sort_by_length, HostPlan& P) {
+                    int sort_by_length, int pack_compartments, HostPlan& P) {
   if (n_cells < 0 || (n_cells > 0 && !ncomp)) return HINES_ERR_INVALID_ARG;
   P = HostPlan();
   P.n_cells = n_cells;
@@ -303,8 +303,12 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
   }
 
   // tasks: per kind, units largest first (ties by cell, then root branch),
-  // packed next-fit while every relative level holds at most kLanes branches
-  // (Section 4's rule with the 32 lanes of a warp)
+  // packed next-fit up to pack_compartments compartments per task (levels of
+  // more than 32 branches become several chunks), or, with the lane rule,
+  // while every relative level holds at most kLanes branches (Section 4's
+  // rule with the 32 lanes of a warp)
+  const bool lane_rule = pack_compartments < 0;
+  const int64_t pack_max = pack_compartments > 0 ? pack_compartments : 16384;
   P.n_tasks = 0;
   P.task_kind.clear();
   P.task_nlvl.clear();
@@ -325,20 +329,26 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
     });
     std::vector<std::vector<int32_t>> groups;
     std::vector<int32_t> cnt, ucnt;
+    int64_t gsize = 0;
     for (int32_t u : us) {
       ucnt.assign((size_t)units[(size_t)u].nlvl, 0);
       for (int32_t b : unit_br[(size_t)u]) ucnt[(size_t)P.br_rlevel[(size_t)b]]++;
       bool fits = !groups.empty();
-      if (fits)
+      if (fits && lane_rule) {
         for (size_t l = 0; l < ucnt.size(); ++l)
           if ((l < cnt.size() ? cnt[l] : 0) + ucnt[l] > kLanes) {
             fits = false;
             break;
           }
+      } else if (fits) {
+        fits = gsize + units[(size_t)u].size <= pack_max;
+      }
       if (!fits) {
         groups.emplace_back();
         cnt.clear();
+        gsize = 0;
       }
+      gsize += units[(size_t)u].size;
       groups.back().push_back(u);
       if (cnt.size() < ucnt.size()) cnt.resize(ucnt.size(), 0);
       for (size_t l = 0; l < ucnt.size(); ++l) cnt[l] += ucnt[l];

@@ -58,6 +58,6 @@ constexpr int64_t kUnitMax = 4096;  // largest unit (compartments); larger cells
 
 // Return codes follow hines_status.
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,
-                    int sort_by_length, HostPlan& out);
+                    int sort_by_length, int pack_compartments, HostPlan& out);
 
 }  // namespace hines

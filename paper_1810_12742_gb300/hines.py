@@ -46,7 +46,8 @@ class HinesError(RuntimeError):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("host_only", ctypes.c_int32), ("split_branches", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
-                ("sort_by_length", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("sort_by_length", ctypes.c_int32), ("pack_compartments", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -112,11 +113,12 @@ class Plan:
     touching the GPU (for inspection)."""
 
     def __init__(self, ncomp, parent, split_branches: bool = False, host_only: bool = False, cta_threads: int = 0,
-                 sort_by_length: bool = False):
+                 sort_by_length: bool = False, pack_compartments: int = 0):
         self._h = ctypes.c_void_p()
         nc = np.ascontiguousarray(ncomp, np.int32)
         pa = np.ascontiguousarray(parent, np.int32)
-        opts = PlanOpts(int(host_only), int(split_branches), int(cta_threads), int(sort_by_length))
+        opts = PlanOpts(int(host_only), int(split_branches), int(cta_threads), int(sort_by_length),
+                        int(pack_compartments))
         _check(lib().hines_plan_create(ctypes.byref(self._h), nc.size, _np_ptr(nc), _np_ptr(pa), ctypes.byref(opts)),
                "hines_plan_create")
         info = PlanInfo()

@@ -45,7 +45,7 @@ def test_argument_errors_without_gpu():
     assert L.hines_plan_create(None, 1, nc.ctypes.data_as(ctypes.c_void_p), pa.ctypes.data_as(ctypes.c_void_p),
                                None) == H.HINES_ERR_INVALID_ARG
     opts = H.PlanOpts(1, 0, 0)
-    opts.reserved[1] = 1
+    opts.reserved[0] = 1
     assert L.hines_plan_create(ctypes.byref(h), 1, nc.ctypes.data_as(ctypes.c_void_p),
                                pa.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts)) == H.HINES_ERR_INVALID_ARG
     opts = H.PlanOpts(1, 0, 48)  # not a multiple of 32
