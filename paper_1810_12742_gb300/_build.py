@@ -41,7 +41,7 @@ def _headers():
 def _digest(extra=()) -> str:
     h = hashlib.sha256()
     for f in _sources() + _headers():
-        h.update(f.encode())
+        h.update(os.path.relpath(f, ROOT).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
     h.update(" ".join(NVCC_FLAGS + CXX_FLAGS + list(extra)).encode())

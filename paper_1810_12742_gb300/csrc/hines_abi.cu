@@ -49,13 +49,14 @@ hines_status upload(hines_plan_t p, int cta_threads) {
     const int32_t cb = H.tchild_ptr[k], ce = H.tchild_ptr[k + 1];
     m.nchild = (int16_t)(ce - cb);
     int32_t lo = INT32_MAX, hi = -1;
+    m.xtask = 0;
     for (int32_t q = cb; q < ce; ++q) {
       lo = std::min(lo, H.tchild[(size_t)q]);
       hi = std::max(hi, H.tchild[(size_t)q]);
+      if (H.br_task[(size_t)H.torder[(size_t)H.tchild[(size_t)q]]] != H.br_task[(size_t)b]) m.xtask = 1;
     }
     m.ccontig = (int16_t)(ce > cb && hi - lo + 1 == ce - cb);
     m.cpos = m.ccontig ? lo : cb;
-    m.pad = 0;
   }
   std::vector<Item> items = {
       {tmeta.data(), tmeta.size() * sizeof(hines::BrMetaT), (const void**)&D.tmeta},
@@ -64,6 +65,9 @@ hines_status upload(hines_plan_t p, int cta_threads) {
       {H.tlvl_ptr.data(), H.tlvl_ptr.size() * 4, (const void**)&D.tlvl_ptr},
       {H.tchild.data(), H.tchild.size() * 4, (const void**)&D.tchild},
       {H.phase_entry.data(), H.phase_entry.size() * 4, (const void**)&D.phase_entry},
+      {H.cell_top_task.data(), H.cell_top_task.size() * 4, (const void**)&D.cell_top_task},
+      {H.counter_init.data(), H.counter_init.size() * 4, (const void**)&D.counter_init},
+      {H.task_sub.data(), H.task_sub.size() * 4, (const void**)&D.task_sub},
       {H.cell_off.data(), H.cell_off.size() * 8, (const void**)&D.cell_off},
       {H.task_cell.data(), H.task_cell.size() * 4, (const void**)&D.task_cell},
       {H.cell_nlvl.data(), H.cell_nlvl.size() * 4, (const void**)&D.cell_nlvl},
@@ -96,8 +100,9 @@ hines_status upload(hines_plan_t p, int cta_threads) {
   }
   const size_t n = (size_t)H.n_unknowns, nb = H.br_first.size(), nc = (size_t)H.n_cells;
   const size_t fac_b = align256(n * 8 + 8), cd_b = align256(nb * 16 + 16), cb_b = align256(nb * 8 + 8),
-               ds_b = align256(nb * 16 + 16), xl_b = align256(nb * 8 + 8), red_b = align256(nc * 8 + 8);
-  const size_t wtotal = fac_b + cd_b + cb_b + ds_b + xl_b + red_b + 256;
+               ds_b = align256(nb * 16 + 16), xl_b = align256(nb * 8 + 8), red_b = align256(nc * 8 + 8),
+               cnt_b = align256((nc + 4) * 4);
+  const size_t wtotal = fac_b + cd_b + cb_b + ds_b + xl_b + red_b + cnt_b;
   if (cudaMalloc(&p->work, wtotal) != cudaSuccess) {
     cudaGetLastError();
     p->work = nullptr;
@@ -118,6 +123,7 @@ hines_status upload(hines_plan_t p, int cta_threads) {
   D.red = w;
   w += red_b;
   D.counter = reinterpret_cast<int32_t*>(w);
+  D.cell_pending = D.counter + 4;
   D.n_wtasks = H.n_tasks;
   for (int k = 0; k < 4; ++k) D.phase_off[k] = H.phase_off.empty() ? 0 : H.phase_off[(size_t)k];
   D.n_cells = H.n_cells;

@@ -14,7 +14,7 @@ struct __align__(16) BrMetaT {
   int16_t len;      // compartments (1..16)
   int16_t nchild;   // children
   int16_t ccontig;  // 1: the children are positions cpos .. cpos + nchild - 1
-  int16_t pad;
+  int16_t xtask;    // 1: some child is in another task (written by another warp in the same launch)
 };
 
 // Device copy of the host plan (pointers into one metadata allocation) and
@@ -44,9 +44,13 @@ struct DevPlan {
   const int32_t* tlvl_ptr = nullptr;      // per task nlvl + 1 positions
   const BrMetaT* tmeta = nullptr;         // [nb] by position
   const int32_t* tchild = nullptr;        // child positions (non-contiguous children)
-  const int32_t* phase_entry = nullptr;   // 4 * task + visits, phases A, B, C concatenated
+  const int32_t* phase_entry = nullptr;   // 4 * task + visits, phases A, B (empty), C concatenated
   int32_t phase_off[4] = {0, 0, 0, 0};
-  int32_t* counter = nullptr;             // [4] work counters (workspace)
+  int32_t* counter = nullptr;             // [4 + n_cells] work counters, then cell_pending (workspace)
+  const int32_t* counter_init = nullptr;  // [4 + n_cells] values restored before every solve
+  const int32_t* cell_top_task = nullptr; // [n_cells] task of the cell's top part, -1 if not cut
+  const int32_t* task_sub = nullptr;      // [2 * n_wtasks] (cell, subtree units) of a subtree task
+  int32_t* cell_pending = nullptr;        // counter + 4: subtree units whose elimination is still to finish
   int32_t grid[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // persistent grid size per kernel kind
   // workspace
   void* fac = nullptr;    // n_unknowns * 8 bytes: factor (FP64 / FP32 solves), FP32 working arrays (refine)

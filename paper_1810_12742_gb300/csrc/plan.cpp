@@ -322,7 +322,10 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
     std::vector<int32_t> us;
     for (size_t u = 0; u < units.size(); ++u)
       if (units[u].kind == kind) us.push_back((int32_t)u);
+    // subtrees are packed per cell (a task finishes at most one cell)
     std::stable_sort(us.begin(), us.end(), [&](int32_t x, int32_t y) {
+      if (kind == 1 && units[(size_t)x].cell != units[(size_t)y].cell)
+        return units[(size_t)x].cell < units[(size_t)y].cell;
       if (units[(size_t)x].size != units[(size_t)y].size) return units[(size_t)x].size > units[(size_t)y].size;
       if (units[(size_t)x].cell != units[(size_t)y].cell) return units[(size_t)x].cell < units[(size_t)y].cell;
       return units[(size_t)x].root < units[(size_t)y].root;
@@ -333,7 +336,8 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
     for (int32_t u : us) {
       ucnt.assign((size_t)units[(size_t)u].nlvl, 0);
       for (int32_t b : unit_br[(size_t)u]) ucnt[(size_t)P.br_rlevel[(size_t)b]]++;
-      bool fits = !groups.empty();
+      bool fits = !groups.empty() && kind != 2;  // top parts are never packed
+      if (fits && kind == 1 && units[(size_t)groups.back()[0]].cell != units[(size_t)u].cell) fits = false;
       if (fits && lane_rule) {
         for (size_t l = 0; l < ucnt.size(); ++l)
           if ((l < cnt.size() ? cnt[l] : 0) + ucnt[l] > kLanes) {
@@ -385,31 +389,51 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
       task_size.push_back(size);
     }
   }
-  // phases: A = whole-cell tasks (both visits) and subtree tasks (elimination),
-  // heaviest first; B = top parts (both visits); C = subtree tasks
-  // (substitution).  Entry = 4 * task + visits (0: both, 1: elimination, 2: substitution).
+  // phases: A = whole-cell tasks (both visits) and subtree tasks
+  // (elimination), heaviest first; a cell's top part runs in phase A too,
+  // taken over by the warp that finishes the cell's last subtree (it has no
+  // list entry); C = subtree tasks (substitution), heaviest first.
+  // Entry = 4 * task + visits (0: both, 1: elimination, 2: substitution).
   {
-    std::vector<int32_t> a, b, c;
+    std::vector<int32_t> a, c;
     for (int32_t t = 0; t < P.n_tasks; ++t) {
       if (P.task_kind[(size_t)t] == 0) a.push_back(4 * t + 0);
       if (P.task_kind[(size_t)t] == 1) {
         a.push_back(4 * t + 1);
         c.push_back(4 * t + 2);
       }
-      if (P.task_kind[(size_t)t] == 2) b.push_back(4 * t + 0);
     }
     auto work = [&](int32_t e) { return task_size[(size_t)(e >> 2)] * ((e & 3) == 0 ? 2 : 1); };
     auto heavy_first = [&](std::vector<int32_t>& v) {
       std::stable_sort(v.begin(), v.end(), [&](int32_t x, int32_t y) { return work(x) > work(y); });
     };
     heavy_first(a);
-    heavy_first(b);
     heavy_first(c);
-    P.phase_off = {0, (int32_t)a.size(), (int32_t)(a.size() + b.size()), (int32_t)(a.size() + b.size() + c.size())};
+    P.phase_off = {0, (int32_t)a.size(), (int32_t)a.size(), (int32_t)(a.size() + c.size())};
     P.phase_entry = a;
-    P.phase_entry.insert(P.phase_entry.end(), b.begin(), b.end());
     P.phase_entry.insert(P.phase_entry.end(), c.begin(), c.end());
   }
+  // top-part hand-over: per cell its top task and number of subtree units;
+  // per subtree task the cells of its units with their counts
+  P.cell_top_task.assign((size_t)n_cells, -1);
+  P.cell_nsub.assign((size_t)n_cells, 0);
+  for (const auto& u : units)
+    if (u.kind == 1) P.cell_nsub[(size_t)u.cell]++;
+  P.counter_init.assign(4, 0);
+  P.counter_init.insert(P.counter_init.end(), P.cell_nsub.begin(), P.cell_nsub.end());
+  for (int64_t b = 0; b < nb; ++b)
+    if (P.br_kind[(size_t)b] == 2) P.cell_top_task[(size_t)P.br_cell[(size_t)b]] = P.br_task[(size_t)b];
+  // per task the cell its subtree units belong to (subtree tasks hold one
+  // cell's units only) and their number; -1 / 0 for other tasks
+  P.task_sub.assign(2 * (size_t)P.n_tasks, 0);
+  for (int32_t t = 0; t < P.n_tasks; ++t) P.task_sub[2 * (size_t)t] = -1;
+  for (const auto& u : units) {
+    if (u.kind != 1) continue;
+    const size_t t = (size_t)P.br_task[(size_t)u.root];
+    P.task_sub[2 * t] = u.cell;
+    P.task_sub[2 * t + 1]++;
+  }
+
   P.tpos.assign((size_t)nb, -1);
   for (size_t k = 0; k < P.torder.size(); ++k) P.tpos[(size_t)P.torder[k]] = (int32_t)k;
   P.tchild_ptr.assign((size_t)nb + 1, 0);

@@ -49,6 +49,11 @@ struct HostPlan {
   // launch phases: entries 4 * task + visits (0 both, 1 elimination, 2 substitution)
   std::vector<int32_t> phase_off;    // [4]
   std::vector<int32_t> phase_entry;
+  // top-part hand-over
+  std::vector<int32_t> cell_top_task;  // [n_cells] task of the cell's top part, -1 if not cut
+  std::vector<int32_t> cell_nsub;      // [n_cells] subtree units of the cell
+  std::vector<int32_t> counter_init;   // [4 + n_cells] work counters (0) then cell_nsub
+  std::vector<int32_t> task_sub;       // [2 * n_tasks] (cell, subtree units) of a subtree task, else (-1, 0)
 };
 
 constexpr int kLanes = 32;       // branches per chunk (one per lane)

@@ -1,18 +1,18 @@
 // Warp-task kernels of the batched Hines solver, sm_103a.
 //
 // The planner cuts every cell into units -- whole small cells, or the top part
-// and the subtrees of a large cell -- and packs units into tasks so that every
-// level of a task (counted from its units' roots) holds at most 32 branches
-// (Section 4's rule with the 32 lanes of a warp).  A warp owns a task and walks
-// its levels, one level = one chunk of at most 32 branches, one per lane:
+// and the subtrees of a large cell -- and packs units into tasks (by size, or
+// by Section 4's rule with the 32 lanes of a warp).  A warp owns a task and
+// walks its levels, one level = chunks of at most 32 branches, one per lane:
 // deepest level first for the elimination, root level first for the
 // substitution (Section 3).  Inside a branch the parent of compartment i is
 // i - 1 (Section 5): each lane runs a Thomas chain (Listing 1) and leaves one
 // contribution for its parent compartment (Listing 2's parent lookup).
 //
-// A solve is three launches: (A) whole-cell tasks (both sweeps) and the
-// elimination of subtree tasks; (B) top parts (both sweeps); (C) the
-// substitution of subtree tasks.  Within a launch no warp waits for another.
+// A solve is two launches: (A) whole-cell tasks (both sweeps), the
+// elimination of subtree tasks and, taken over by the warp that finishes a
+// cell's last subtree, that cell's top part (both sweeps); (C) the
+// substitution of subtree tasks.  No warp ever waits for another.
 //
 // The levels of a task follow one another in the same warp, so a chunk's
 // children are the lanes of the chunk just before it (elimination) and its
@@ -39,15 +39,16 @@ using namespace dev;
 constexpr int kL = kBranchCap;      // compartments per branch, at most
 constexpr int kSlots = 32 * kL;     // one staged array of one chunk
 constexpr int kWarps = kWarpsPerCta;
+constexpr int kSmemPerSm = 227 * 1024;  // shared memory one SM gives its CTAs
 
 struct Meta {
   long long first, pcomp;
-  int ppos, cpos, len, nchild, ccontig;
+  int ppos, cpos, len, nchild, ccontig, xtask;
   float4 ds;  // compensated substitution: folded distal state left by the elimination
 };
 
 __device__ __forceinline__ Meta load_meta(const DevPlan& P, int pos, bool valid, bool want_ds) {
-  Meta m{0, -1, -1, 0, 0, 0, 0, make_float4(0.f, 0.f, 0.f, 0.f)};
+  Meta m{0, -1, -1, 0, 0, 0, 0, 0, make_float4(0.f, 0.f, 0.f, 0.f)};
   if (valid) {
     if (want_ds) m.ds = static_cast<const float4*>(P.dstate)[pos];
     const BrMetaT t = P.tmeta[pos];
@@ -58,12 +59,20 @@ __device__ __forceinline__ Meta load_meta(const DevPlan& P, int pos, bool valid,
     m.len = t.len;
     m.nchild = t.nchild;
     m.ccontig = t.ccontig;
+    m.xtask = t.xtask;
   }
   return m;
 }
 
 __device__ __forceinline__ int child_pos(const DevPlan& P, const Meta& m, int i) {
   return m.ccontig ? m.cpos + i : __ldg(P.tchild + m.cpos + i);
+}
+
+// A child's contribution slot: through L2 when another warp may have written
+// it in this launch (a top part's subtree children), else the ordinary path.
+template <typename V>
+__device__ __forceinline__ V slot_load(const V* p, const Meta& m) {
+  return m.xtask ? __ldcg(p) : *p;
 }
 
 // The chunk processed just before the current one in the same sweep.
@@ -101,6 +110,7 @@ struct CompMode {
   static constexpr int kStageBytes = 3 * kSlots * 4;
   static constexpr int kCacheBytes = 2 * 32 * 16 + 2 * 32 * 8;
   static constexpr int kWarpBytes = 2 * kStageBytes + kCacheBytes;
+  static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);  // CTAs per SM that shared memory allows
 
   static constexpr bool kWantDs = true;
 
@@ -136,7 +146,7 @@ struct CompMode {
       for (int i = 0; i < m.nchild; ++i) {
         const int cp = child_pos(P, m, i);
         const int loc = cp - pv.c0;
-        const float4 v = (loc >= 0 && loc < pv.n) ? cslot[pv.which * 32 + loc] : slot[cp];
+        const float4 v = (loc >= 0 && loc < pv.n) ? cslot[pv.which * 32 + loc] : slot_load(slot + cp, m);
         Dv = ff_sub(Dv, v.x, v.y);
         Bv = ff_sub(Bv, v.z, v.w);
       }
@@ -252,6 +262,7 @@ struct FactorMode {
   static constexpr int kStageBytes = 3 * kSlots * (int)sizeof(T);
   static constexpr int kCacheBytes = 2 * 32 * 2 * (int)sizeof(T) + 2 * 32 * (int)sizeof(T);
   static constexpr int kWarpBytes = 2 * kStageBytes + kCacheBytes;
+  static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);  // CTAs per SM that shared memory allows
 
   static constexpr bool kWantDs = false;
 
@@ -308,8 +319,8 @@ struct FactorMode {
         const int cp = child_pos(P, m, i);
         const int loc = cp - pv.c0;
         const bool local = loc >= 0 && loc < pv.n;
-        D -= local ? cslot[(pv.which * 32 + loc) * 2] : slot[2 * cp];
-        B -= local ? cslot[(pv.which * 32 + loc) * 2 + 1] : slot[2 * cp + 1];
+        D -= local ? cslot[(pv.which * 32 + loc) * 2] : slot_load(slot + 2 * cp, m);
+        B -= local ? cslot[(pv.which * 32 + loc) * 2 + 1] : slot_load(slot + 2 * cp + 1, m);
       }
       for (int k = 0; k < len - 1; ++k) {
         const T uk = su[sidx(k, lane)];
@@ -447,19 +458,51 @@ __device__ void run_task(const DevPlan& P, const typename M::Args& A, int t, int
   }
 }
 
+// After a subtree task's elimination: count its units off their cell's
+// pending count; the warp that finishes the cell's last subtree takes over
+// the cell's top part (both visits) as its next task.  Nothing waits: the
+// hand-over goes to whoever arrives last.  Release: every lane fences its slot
+// writes before lane 0's atomic; acquire: the fence after it, and the top
+// part reads those slots through L2.  Returns the top task, or -1.
+__device__ __forceinline__ int hand_over(const DevPlan& P, int t, int lane) {
+  __threadfence();
+  __syncwarp();
+  const int cell = __ldg(P.task_sub + 2 * t);
+  if (cell < 0) return -1;
+  int last = 0;
+  if (lane == 0) {
+    const int cnt = __ldg(P.task_sub + 2 * t + 1);
+    last = atomicSub(P.cell_pending + cell, cnt) == cnt;
+  }
+  if (!__shfl_sync(kFull, last, 0)) return -1;
+  __threadfence();
+  return __ldg(P.cell_top_task + cell);
+}
+
 template <class M>
-__global__ void __launch_bounds__(32 * kWarps) k_units(DevPlan P, typename M::Args A, int phase) {
+__global__ void __launch_bounds__(32 * kWarps, M::kMinBlocks) k_units(DevPlan P, typename M::Args A, int phase) {
   extern __shared__ __align__(16) unsigned char smem_u[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* wbase = smem_u + w * M::kWarpBytes;
   const int e0 = P.phase_off[phase], ne = P.phase_off[phase + 1] - e0;
+  int next = -1;  // a top part handed over to this warp
   for (;;) {
-    int k = 0;
-    if (lane == 0) k = atomicAdd(P.counter + phase, 1);
-    k = __shfl_sync(kFull, k, 0);
-    if (k >= ne) break;
-    const int e = P.phase_entry[e0 + k];
-    run_task<M>(P, A, e >> 2, e & 3, lane, wbase);
+    int t, code;
+    if (next >= 0) {
+      t = next;
+      code = 0;
+      next = -1;
+    } else {
+      int k = 0;
+      if (lane == 0) k = atomicAdd(P.counter + phase, 1);
+      k = __shfl_sync(kFull, k, 0);
+      if (k >= ne) break;
+      const int e = P.phase_entry[e0 + k];
+      t = e >> 2;
+      code = e & 3;
+    }
+    run_task<M>(P, A, t, code, lane, wbase);
+    if (code == 1) next = hand_over(P, t, lane);
   }
 }
 
@@ -480,7 +523,9 @@ template <class M>
 cudaError_t launch_phases(const DevPlan& P, const typename M::Args& A, int grid, cudaStream_t s) {
   if (P.n_wtasks == 0) return cudaSuccess;
   const size_t smem = (size_t)kWarps * M::kWarpBytes;
-  cudaError_t e = cudaMemsetAsync(P.counter, 0, 4 * sizeof(int32_t), s);
+  // work counters to 0 and per-cell subtree counts to their full values
+  cudaError_t e = cudaMemcpyAsync(P.counter, P.counter_init, (4 + (size_t)P.n_cells) * sizeof(int32_t),
+                                  cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   for (int phase = 0; phase < 3; ++phase) {
     const int ne = P.phase_off[phase + 1] - P.phase_off[phase];

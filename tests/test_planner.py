@@ -127,12 +127,17 @@ def py_tasks(ncomp, units, sort_by_length, pack=16384):
     tasks = []
     for kind in (0, 1, 2):
         us = [u for u in units if u[0] == kind]
-        us.sort(key=lambda u: (-sum(G["len"][b] for b in u[3]), u[1], u[2]))
+        if kind == 1:  # subtrees packed per cell
+            us.sort(key=lambda u: (u[1], -sum(G["len"][b] for b in u[3]), u[2]))
+        else:
+            us.sort(key=lambda u: (-sum(G["len"][b] for b in u[3]), u[1], u[2]))
         groups, cnt, gsize = [], [], 0
         for u in us:
             cc = np.bincount([rl[b] for b in u[3]])
             usize = sum(G["len"][b] for b in u[3])
-            if pack < 0:  # Section 4's rule: every level at most 32 branches
+            if kind == 2 or (kind == 1 and groups and groups[-1][0][1] != u[1]):
+                fits = False  # a top part alone; subtrees of one cell per task
+            elif pack < 0:  # Section 4's rule: every level at most 32 branches
                 fits = bool(groups) and all((cnt[l] if l < len(cnt) else 0) + cc[l] <= LANES for l in range(len(cc)))
             else:
                 fits = bool(groups) and gsize + usize <= pack
