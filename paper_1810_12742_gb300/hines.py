@@ -283,19 +283,36 @@ def cable_loss_seed(plan: Plan, V, target, vbar):
                                        _dptr(vbar, f, n, "vbar"), _stream()), "hines_cable_loss_seed")
 
 
+def _host_staging(plan: Plan):
+    """Device staging buffers (d, u, b in FP32, x in FP64) owned by the plan object."""
+    torch = _torch()
+    st = getattr(plan, "_staging", None)
+    if st is None:
+        n = plan.n_unknowns
+        st = tuple(torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)) + (
+            torch.empty(n, dtype=torch.float64, device="cuda"),)
+        plan._staging = st
+    return st
+
+
 def solve_refine_host(plan: Plan, d, u, b, x, steps: int = 2):
     """solve_refine on host tensors (pinned for asynchronous copies): copies d,
     u, b to device staging buffers owned by the plan object, solves, and copies
     x back, all on the current stream."""
-    torch = _torch()
-    n = plan.n_unknowns
-    st = getattr(plan, "_staging", None)
-    if st is None:
-        st = tuple(torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)) + (
-            torch.empty(n, dtype=torch.float64, device="cuda"),)
-        plan._staging = st
+    st = _host_staging(plan)
     for dst, src in zip(st[:3], (d, u, b)):
         dst.copy_(src, non_blocking=True)
     solve_refine(plan, st[0], st[1], st[2], st[3], steps)
+    x.copy_(st[3], non_blocking=True)
+    return x
+
+
+def solve_compensated_host(plan: Plan, d, u, b, x):
+    """solve_compensated on host tensors (pinned for asynchronous copies), with
+    the same staging as solve_refine_host."""
+    st = _host_staging(plan)
+    for dst, src in zip(st[:3], (d, u, b)):
+        dst.copy_(src, non_blocking=True)
+    solve_compensated(plan, st[0], st[1], st[2], st[3])
     x.copy_(st[3], non_blocking=True)
     return x
