@@ -86,6 +86,7 @@ typedef struct {
   int64_t n_branches;       /* unbranched runs after optional splitting */
   int64_t workspace_bytes;  /* device workspace owned by the plan */
   int64_t metadata_bytes;   /* device metadata owned by the plan */
+  int64_t n_packed;         /* length of a solver-layout array (n_unknowns plus block padding) */
 } hines_plan_info_t;
 
 /*
@@ -150,6 +151,44 @@ hines_status hines_plan_export(hines_plan_t plan, int64_t *first, int64_t *len, 
  */
 hines_status hines_plan_export_tasks(hines_plan_t plan, int64_t *branch_task, int64_t *branch_kind,
                                      int64_t *task_order);
+
+/*
+ * The solver layout (Section 5: the data of the branches a warp solves
+ * together, interleaved so that each step reads one contiguous run).  Every
+ * chunk -- at most 32 branches of one level of a warp task, one per lane --
+ * owns a block starting on a multiple of 4 slots; row r of the block holds
+ * the r-th compartment counted from the distal end of every branch of the
+ * chunk longer than r, in lane order.  A solver-layout array has
+ * info.n_packed elements (n_unknowns plus padding slots) and must be
+ * 16-byte aligned.
+ *
+ * hines_plan_export_packed: host int64[n_packed], the natural-layout index
+ * held by each slot, -1 for a padding slot.
+ */
+hines_status hines_plan_export_packed(hines_plan_t plan, int64_t *slot_natural);
+
+/*
+ * Permute one array between the layouts (device arrays; elem_bytes 4 or 8).
+ * hines_pack writes every slot of packed[n_packed] (padding slots: zero) from
+ * natural[n_unknowns]; hines_unpack writes natural[n_unknowns] from the
+ * non-padding slots of packed.  Stream-ordered.
+ */
+hines_status hines_pack(hines_plan_t plan, int32_t elem_bytes, const void *natural, void *packed,
+                        hines_stream_t stream);
+hines_status hines_unpack(hines_plan_t plan, int32_t elem_bytes, const void *packed, void *natural,
+                          hines_stream_t stream);
+
+/*
+ * hines_solve and hines_solve_compensated on solver-layout arrays (each
+ * n_packed elements, 16-byte aligned; padding slots are read and ignored,
+ * and padding slots of the output are left unspecified).  The arithmetic is
+ * the same; only where each value lives differs, so a batch kept in the
+ * solver layout between solves (a simulation's state) needs no permutation.
+ */
+hines_status hines_solve_packed(hines_plan_t plan, int32_t dtype, const void *d, const void *u, void *b_inout,
+                                hines_stream_t stream);
+hines_status hines_solve_compensated_packed(hines_plan_t plan, const float *d, const float *u, const float *b,
+                                            double *x_out, hines_stream_t stream);
 
 /*
  * Solve A x = b for every cell (Section 2, Listing 2), in place.

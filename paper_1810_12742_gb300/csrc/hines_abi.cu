@@ -58,8 +58,16 @@ hines_status upload(hines_plan_t p, int cta_threads) {
     m.ccontig = (int16_t)(ce > cb && hi - lo + 1 == ce - cb);
     m.cpos = m.ccontig ? lo : cb;
   }
+  // solver layout: per position (block offset, parent's solver-layout index)
+  std::vector<int64_t> pkm(2 * H.torder.size());
+  for (size_t k = 0; k < H.torder.size(); ++k) {
+    pkm[2 * k] = H.pk_blk[k];
+    pkm[2 * k + 1] = H.pk_pcomp[k];
+  }
   std::vector<Item> items = {
       {tmeta.data(), tmeta.size() * sizeof(hines::BrMetaT), (const void**)&D.tmeta},
+      {pkm.data(), pkm.size() * 8, (const void**)&D.pk_meta},
+      {H.pk_perm.data(), H.pk_perm.size() * 8, (const void**)&D.pk_perm},
       {H.task_nlvl.data(), H.task_nlvl.size() * 4, (const void**)&D.task_nlvl},
       {H.task_lvl_off.data(), H.task_lvl_off.size() * 8, (const void**)&D.task_lvl_off},
       {H.tlvl_ptr.data(), H.tlvl_ptr.size() * 4, (const void**)&D.tlvl_ptr},
@@ -99,7 +107,9 @@ hines_status upload(hines_plan_t p, int cta_threads) {
     off += align256(it.bytes > 0 ? it.bytes : 1);
   }
   const size_t n = (size_t)H.n_unknowns, nb = H.br_first.size(), nc = (size_t)H.n_cells;
-  const size_t fac_b = align256(n * 8 + 8), cd_b = align256(nb * 16 + 16), cb_b = align256(nb * 8 + 8),
+  // the factor is indexed by natural or solver-layout position
+  const size_t fac_b = align256(std::max(n, (size_t)H.n_packed) * 8 + 8), cd_b = align256(nb * 16 + 16),
+               cb_b = align256(nb * 8 + 8),
                ds_b = align256(nb * 16 + 16), xl_b = align256(nb * 8 + 8), red_b = align256(nc * 8 + 8),
                cnt_b = align256((nc + 4) * 4);
   const size_t wtotal = fac_b + cd_b + cb_b + ds_b + xl_b + red_b + cnt_b;
@@ -125,6 +135,7 @@ hines_status upload(hines_plan_t p, int cta_threads) {
   D.counter = reinterpret_cast<int32_t*>(w);
   D.cell_pending = D.counter + 4;
   D.n_wtasks = H.n_tasks;
+  D.n_packed = H.n_packed;
   for (int k = 0; k < 4; ++k) D.phase_off[k] = H.phase_off.empty() ? 0 : H.phase_off[(size_t)k];
   D.n_cells = H.n_cells;
   D.n_tasks = H.n_cells;
@@ -225,6 +236,7 @@ hines_status hines_plan_info(hines_plan_t p, hines_plan_info_t* info) {
   info->n_branches = (int64_t)p->host.br_first.size();
   info->workspace_bytes = p->work_bytes;
   info->metadata_bytes = p->meta_bytes;
+  info->n_packed = p->host.n_packed;
   return HINES_OK;
 }
 
@@ -276,6 +288,56 @@ hines_status hines_solve_compensated(hines_plan_t p, const float* d, const float
   if (!need(p, d) || !need(p, u) || !need(p, b) || !need(p, x_out)) return HINES_ERR_INVALID_ARG;
   return launched(
       hines::launch_unit_solve_compensated(p->dev, d, u, b, x_out, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+// Solver-layout arrays: n_packed elements, 16-byte aligned (blocks are copied
+// with 16-byte transfers).
+bool need_pk(hines_plan_t p, const void* a) {
+  if (p->host.n_packed == 0) return true;
+  return a != nullptr && (reinterpret_cast<uintptr_t>(a) & 15u) == 0;
+}
+
+hines_status hines_plan_export_packed(hines_plan_t p, int64_t* slot_natural) {
+  if (!p || (!slot_natural && p->host.n_packed > 0)) return HINES_ERR_INVALID_ARG;
+  for (size_t k = 0; k < p->host.pk_perm.size(); ++k) slot_natural[k] = p->host.pk_perm[k];
+  return HINES_OK;
+}
+
+hines_status hines_pack(hines_plan_t p, int32_t elem_bytes, const void* natural, void* packed, hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if ((elem_bytes != 4 && elem_bytes != 8) || !need(p, natural) || !need_pk(p, packed)) return HINES_ERR_INVALID_ARG;
+  return launched(hines::launch_pack(p->dev, elem_bytes, natural, packed, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+hines_status hines_unpack(hines_plan_t p, int32_t elem_bytes, const void* packed, void* natural,
+                          hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if ((elem_bytes != 4 && elem_bytes != 8) || !need(p, natural) || !need_pk(p, packed)) return HINES_ERR_INVALID_ARG;
+  return launched(hines::launch_unpack(p->dev, elem_bytes, packed, natural, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+hines_status hines_solve_packed(hines_plan_t p, int32_t dtype, const void* d, const void* u, void* b_inout,
+                                hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need_pk(p, d) || !need_pk(p, u) || !need_pk(p, b_inout)) return HINES_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (dtype == HINES_F64)
+    return launched(hines::launch_pk_solve_f64(p->dev, (const double*)d, (const double*)u, (double*)b_inout, s));
+  if (dtype == HINES_F32)
+    return launched(hines::launch_pk_solve_f32(p->dev, (const float*)d, (const float*)u, (float*)b_inout, s));
+  return HINES_ERR_INVALID_ARG;
+}
+
+hines_status hines_solve_compensated_packed(hines_plan_t p, const float* d, const float* u, const float* b,
+                                            double* x_out, hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need_pk(p, d) || !need_pk(p, u) || !need_pk(p, b) || !need_pk(p, x_out)) return HINES_ERR_INVALID_ARG;
+  return launched(
+      hines::launch_pk_solve_compensated(p->dev, d, u, b, x_out, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 hines_status hines_solve_refine(hines_plan_t p, const float* d, const float* u, const float* b, double* x_out,

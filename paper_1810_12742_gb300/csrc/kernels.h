@@ -51,6 +51,10 @@ struct DevPlan {
   const int32_t* cell_top_task = nullptr; // [n_cells] task of the cell's top part, -1 if not cut
   const int32_t* task_sub = nullptr;      // [2 * n_wtasks] (cell, subtree units) of a subtree task
   int32_t* cell_pending = nullptr;        // counter + 4: subtree units whose elimination is still to finish
+  // solver layout (Section 5's interleaving per chunk)
+  int64_t n_packed = 0;
+  const longlong2* pk_meta = nullptr;     // [nb] per position: (chunk block offset, parent's solver-layout index)
+  const int64_t* pk_perm = nullptr;       // [n_packed] natural index of each solver-layout slot, -1 for padding
   int32_t grid[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // persistent grid size per kernel kind
   // workspace
   void* fac = nullptr;    // n_unknowns * 8 bytes: factor (FP64 / FP32 solves), FP32 working arrays (refine)
@@ -71,6 +75,14 @@ cudaError_t launch_unit_solve_compensated(const DevPlan& P, const float* d, cons
                                           cudaStream_t s);
 cudaError_t launch_unit_cable(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
                               double dt, double E, int theta, bool rhs_from_V, cudaStream_t s);
+
+cudaError_t launch_pk_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s);
+cudaError_t launch_pk_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s);
+cudaError_t launch_pk_solve_compensated(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
+                                        cudaStream_t s);
+// Natural <-> solver layout permutations (elem_bytes 4 or 8).
+cudaError_t launch_pack(const DevPlan& P, int elem_bytes, const void* natural, void* packed, cudaStream_t s);
+cudaError_t launch_unpack(const DevPlan& P, int elem_bytes, const void* packed, void* natural, cudaStream_t s);
 
 // CTA-per-cell kernels (hines_kernels.cu).
 cudaError_t launch_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s);

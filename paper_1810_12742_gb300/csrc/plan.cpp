@@ -444,6 +444,56 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
     int32_t w = P.tchild_ptr[k];
     for (int32_t c = P.child_ptr[(size_t)b]; c < P.child_ptr[(size_t)b + 1]; ++c) P.tchild[(size_t)w++] = P.tpos[(size_t)P.child[(size_t)c]];
   }
+  // solver layout: blocks in task order, levels ascending, chunks of 32
+  {
+    std::vector<int32_t> chunk_c0((size_t)nb, 0);
+    P.pk_blk.assign((size_t)nb, 0);
+    int64_t off = 0;
+    for (int32_t t = 0; t < P.n_tasks; ++t) {
+      const int32_t* lp = P.tlvl_ptr.data() + P.task_lvl_off[(size_t)t];
+      for (int32_t l = 0; l < P.task_nlvl[(size_t)t]; ++l) {
+        for (int32_t c0 = lp[l]; c0 < lp[l + 1]; c0 += kLanes) {
+          const int32_t c1 = std::min(c0 + kLanes, lp[l + 1]);
+          int64_t e = 0;
+          for (int32_t q = c0; q < c1; ++q) {
+            e += P.br_len[(size_t)P.torder[(size_t)q]];
+            P.pk_blk[(size_t)q] = off;
+            chunk_c0[(size_t)q] = c0;
+          }
+          off += (e + kPackAlign - 1) / kPackAlign * kPackAlign;
+        }
+      }
+    }
+    P.n_packed = off;
+    P.pk_perm.assign((size_t)off, -1);
+    P.pk_pcomp.assign((size_t)nb, -1);
+    for (int32_t q = 0; q < (int32_t)nb; ++q) {
+      const int32_t pb = P.br_parent[(size_t)P.torder[(size_t)q]];
+      if (pb >= 0) {
+        const int32_t pq = P.tpos[(size_t)pb];
+        P.pk_pcomp[(size_t)q] = P.pk_blk[(size_t)pq] + (pq - chunk_c0[(size_t)pq]);  // row 0, every lane present
+      }
+    }
+    for (int32_t q = 0; q < (int32_t)nb;) {
+      const int32_t c0 = q;
+      int32_t c1 = q;
+      while (c1 < (int32_t)nb && chunk_c0[(size_t)c1] == c0) ++c1;
+      int64_t row_off = 0;
+      for (int32_t r = 0; r < kBranchCap; ++r) {
+        int64_t rank = 0;
+        for (int32_t j = c0; j < c1; ++j) {
+          const int32_t b = P.torder[(size_t)j];
+          const int32_t len = P.br_len[(size_t)b];
+          if (len > r) {
+            P.pk_perm[(size_t)(P.pk_blk[(size_t)c0] + row_off + rank)] = P.br_first[(size_t)b] + (len - 1 - r);
+            ++rank;
+          }
+        }
+        row_off += rank;
+      }
+      q = c1;
+    }
+  }
   return HINES_OK;
 }
 

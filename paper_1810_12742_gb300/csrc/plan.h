@@ -54,12 +54,23 @@ struct HostPlan {
   std::vector<int32_t> cell_nsub;      // [n_cells] subtree units of the cell
   std::vector<int32_t> counter_init;   // [4 + n_cells] work counters (0) then cell_nsub
   std::vector<int32_t> task_sub;       // [2 * n_tasks] (cell, subtree units) of a subtree task, else (-1, 0)
+
+  // Solver layout (Section 5's interleaving, per chunk): each chunk -- at
+  // most 32 consecutive positions of one task level -- owns a block; row r of
+  // the block holds the r-th compartment from the distal end of every branch
+  // of the chunk longer than r, in lane order, so a warp reads a row as one
+  // contiguous run.  Blocks start on multiples of kPackAlign compartments.
+  int64_t n_packed = 0;
+  std::vector<int64_t> pk_blk;    // [nb] block offset of the chunk of each position
+  std::vector<int64_t> pk_pcomp;  // [nb] solver-layout index of the parent branch's distal compartment, -1 at a root
+  std::vector<int64_t> pk_perm;   // [n_packed] natural index held by each solver-layout slot, -1 for padding
 };
 
 constexpr int kLanes = 32;       // branches per chunk (one per lane)
 constexpr int kBranchCap = 16;   // maximum compartments per branch after capping
 constexpr int kWarpsPerCta = 4;  // warps per CTA of the task kernels (each warp runs its own task)
 constexpr int64_t kUnitMax = 4096;  // largest unit (compartments); larger cells are cut
+constexpr int64_t kPackAlign = 4;   // solver-layout blocks start on multiples of 4 compartments
 
 // Return codes follow hines_status.
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,

@@ -42,18 +42,25 @@ constexpr int kWarps = kWarpsPerCta;
 constexpr int kSmemPerSm = 227 * 1024;  // shared memory one SM gives its CTAs
 
 struct Meta {
-  long long first, pcomp;
+  long long first, pcomp;  // solver layout: the chunk's block offset, the parent's solver-layout index
   int ppos, cpos, len, nchild, ccontig, xtask;
   float4 ds;  // compensated substitution: folded distal state left by the elimination
 };
 
+template <bool kPk>
 __device__ __forceinline__ Meta load_meta(const DevPlan& P, int pos, bool valid, bool want_ds) {
   Meta m{0, -1, -1, 0, 0, 0, 0, 0, make_float4(0.f, 0.f, 0.f, 0.f)};
   if (valid) {
     if (want_ds) m.ds = static_cast<const float4*>(P.dstate)[pos];
     const BrMetaT t = P.tmeta[pos];
-    m.first = t.first;
-    m.pcomp = t.pcomp;
+    if (kPk) {
+      const longlong2 q = P.pk_meta[pos];
+      m.first = q.x;
+      m.pcomp = q.y;
+    } else {
+      m.first = t.first;
+      m.pcomp = t.pcomp;
+    }
     m.ppos = t.ppos;
     m.cpos = t.cpos;
     m.len = t.len;
@@ -93,6 +100,66 @@ __device__ __forceinline__ void for_branch_elements(const Meta& m, int n, int la
   }
 }
 
+// Staged-chunk index of row k (counted from the distal end) of a lane's branch.
+// Natural layout: the XOR-swizzled interleaving built while staging.
+struct NatIdx {
+  __device__ __forceinline__ int operator()(int k, int lane) const { return sidx(k, lane); }
+};
+// Solver layout: the chunk's block as stored, row r holding the lanes whose
+// branch is longer than r, in lane order: offset of row r plus the rank of the
+// lane among them.  Consecutive active lanes read consecutive words.
+struct PkIdx {
+  const uint2* tab;  // per row: (lanes present, row offset)
+  unsigned lt;       // mask of the lanes below this one
+  __device__ __forceinline__ int operator()(int k, int) const {
+    const uint2 t = tab[k];
+    return (int)t.y + __popc(t.x & lt);
+  }
+};
+constexpr int kTabBytes = kL * 8;
+
+// Builds the row table of the current chunk (every lane of the warp calls it).
+__device__ __forceinline__ PkIdx pk_index(const Meta& m, int n, int lane, unsigned char* tabmem) {
+  uint2* tab = reinterpret_cast<uint2*>(tabmem);
+  const int len = lane < n ? m.len : 0;
+  unsigned off = 0;
+#pragma unroll
+  for (int r = 0; r < kL; ++r) {
+    const unsigned mk = __ballot_sync(kFull, len > r);
+    if (lane == r) tab[r] = make_uint2(mk, off);
+    off += __popc(mk);
+  }
+  __syncwarp();
+  return PkIdx{tab, (1u << lane) - 1u};
+}
+
+template <bool kPk>
+struct IdxOf;
+template <>
+struct IdxOf<false> {
+  using type = NatIdx;
+  __device__ static NatIdx make(const Meta&, int, int, unsigned char*) { return NatIdx{}; }
+};
+template <>
+struct IdxOf<true> {
+  using type = PkIdx;
+  __device__ static PkIdx make(const Meta& m, int n, int lane, unsigned char* t) { return pk_index(m, n, lane, t); }
+};
+
+// Solver layout: compartments in the chunk's block (every lane calls it).
+__device__ __forceinline__ int chunk_elems(const Meta& m, int n, int lane) {
+  return __reduce_add_sync(kFull, lane < n ? m.len : 0);
+}
+
+// Solver layout: copy the chunk's block of one array into shared memory with
+// 16-byte copies (blocks start on multiples of 4 compartments and are padded).
+template <typename T>
+__device__ __forceinline__ void stage_block(T* dst, const T* src, long long blk, int e, int lane) {
+  constexpr int V = 16 / (int)sizeof(T);
+  const int nv = (e + V - 1) / V;
+  for (int v = lane; v < nv; v += 32) cp_async16(dst + v * V, src + blk + (long long)v * V);
+}
+
 // ============================================================================
 // Compensated mode: FP32 inputs, double-float arithmetic from FP32 error-free
 // transformations, FP64 solution.  The elimination keeps nothing per
@@ -100,7 +167,9 @@ __device__ __forceinline__ void for_branch_elements(const Meta& m, int n, int la
 // root's solution) and its folded distal state; the substitution re-stages the
 // chunk and re-eliminates it from that state before substituting.
 // ============================================================================
-struct CompMode {
+template <bool kPk>
+struct CompModeT {
+  static constexpr bool kPacked = kPk;
   struct Args {
     const float* d;
     const float* u;
@@ -108,7 +177,7 @@ struct CompMode {
     double* x;
   };
   static constexpr int kStageBytes = 3 * kSlots * 4;
-  static constexpr int kCacheBytes = 2 * 32 * 16 + 2 * 32 * 8;
+  static constexpr int kCacheBytes = 2 * 32 * 16 + 2 * 32 * 8 + kTabBytes;
   static constexpr int kWarpBytes = 2 * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);  // CTAs per SM that shared memory allows
 
@@ -119,12 +188,20 @@ struct CompMode {
     float* sd = reinterpret_cast<float*>(buf);
     float* su = sd + kSlots;
     float* sb = su + kSlots;
-    for_branch_elements<float>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
-      const int q = sidx(lj - 1 - t, jj);
-      cp_async4(&sd[q], A.d + fj + t);
-      cp_async4(&su[q], A.u + fj + t);
-      cp_async4(&sb[q], A.b + fj + t);
-    });
+    if (kPk) {
+      const long long blk = __shfl_sync(kFull, m.first, 0);
+      const int e = chunk_elems(m, n, lane);
+      stage_block(sd, A.d, blk, e, lane);
+      stage_block(su, A.u, blk, e, lane);
+      stage_block(sb, A.b, blk, e, lane);
+    } else {
+      for_branch_elements<float>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+        const int q = sidx(lj - 1 - t, jj);
+        cp_async4(&sd[q], A.d + fj + t);
+        cp_async4(&su[q], A.u + fj + t);
+        cp_async4(&sb[q], A.b + fj + t);
+      });
+    }
     cp_commit();
   }
 
@@ -138,11 +215,12 @@ struct CompMode {
     float4* slot = static_cast<float4*>(P.cd);
     float4* dst = static_cast<float4*>(P.dstate);
     float2* xlast = static_cast<float2*>(P.xlast);
+    const auto Q = IdxOf<kPk>::make(m, n, lane, cache + 2 * 32 * 16 + 2 * 32 * 8);
     if (lane >= n) return;
     const int pos = c0 + lane;
     const int len = m.len;
     if (visit == 0) {
-      ff Dv = {sd[sidx(0, lane)], 0.f}, Bv = {sb[sidx(0, lane)], 0.f};
+      ff Dv = {sd[Q(0, lane)], 0.f}, Bv = {sb[Q(0, lane)], 0.f};
       for (int i = 0; i < m.nchild; ++i) {
         const int cp = child_pos(P, m, i);
         const int loc = cp - pv.c0;
@@ -152,16 +230,16 @@ struct CompMode {
       }
       dst[pos] = make_float4(Dv.h, Dv.l, Bv.h, Bv.l);
       for (int k = 0; k < len - 1; ++k) {
-        const float uk = su[sidx(k, lane)];
+        const float uk = su[Q(k, lane)];
         const ff f = ff_div_f(uk, Dv);
         const ff fu = ff_mul_f(f, uk);
         const ff fb = ff_mul(f, Bv);
-        Dv = ff_sub_dom(sd[sidx(k + 1, lane)], fu.h, fu.l);
-        Bv = ff_sub({sb[sidx(k + 1, lane)], 0.f}, fb.h, fb.l);
+        Dv = ff_sub_dom(sd[Q(k + 1, lane)], fu.h, fu.l);
+        Bv = ff_sub({sb[Q(k + 1, lane)], 0.f}, fb.h, fb.l);
       }
       float4 out;
       if (m.pcomp >= 0) {
-        const float uk = su[sidx(len - 1, lane)];
+        const float uk = su[Q(len - 1, lane)];
         const ff f = ff_div_f(uk, Dv);
         const ff fu = ff_mul_f(f, uk);
         const ff fb = ff_mul(f, Bv);
@@ -179,7 +257,7 @@ struct CompMode {
 #pragma unroll
     for (int k = 0; k < kL; ++k) {
       if (k < len) {
-        const int q = sidx(k, lane);
+        const int q = Q(k, lane);
         sd[q] = Dv.h;
         el[k] = Dv.l;
         sb[q] = Bv.h;
@@ -189,7 +267,7 @@ struct CompMode {
           const ff f = ff_div_f(uk, Dv);
           const ff fu = ff_mul_f(f, uk);
           const ff fb = ff_mul(f, Bv);
-          const int q1 = sidx(k + 1, lane);
+          const int q1 = Q(k + 1, lane);
           Dv = ff_sub_dom(sd[q1], fu.h, fu.l);
           Bv = ff_sub({sb[q1], 0.f}, fb.h, fb.l);
         }
@@ -204,7 +282,7 @@ struct CompMode {
 #pragma unroll
     for (int k = kL - 1; k >= 0; --k) {
       if (k < len) {
-        const int q = sidx(k, lane);
+        const int q = Q(k, lane);
         ff xi;
         if (m.pcomp < 0 && k == len - 1) {
           const float4 t = slot[pos];
@@ -233,6 +311,12 @@ struct CompMode {
     if (visit == 0) return;
     const float* sd = reinterpret_cast<const float*>(buf);
     const float* sb = sd + 2 * kSlots;
+    if (kPk) {
+      const long long blk = __shfl_sync(kFull, m.first, 0);
+      const int e = chunk_elems(m, n, lane);
+      for (int i = lane; i < e; i += 32) A.x[blk + i] = __hiloint2double(__float_as_int(sb[i]), __float_as_int(sd[i]));
+      return;
+    }
     for_branch_elements<float>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
       const int q = sidx(lj - 1 - t, jj);
       A.x[fj + t] = __hiloint2double(__float_as_int(sb[q]), __float_as_int(sd[q]));
@@ -248,8 +332,10 @@ struct CompMode {
 // d_i = s_i (1 + theta dt g_i) + sum of a over the edges at i (a = -u),
 // b_i = s_i V_i + s_i dt g_i (E - (1 - theta) V_i).
 // ============================================================================
-template <typename T, bool kCable>
+template <typename T, bool kCable, bool kPk>
 struct FactorMode {
+  static_assert(!(kCable && kPk), "the cable rebuild runs in the natural layout");
+  static constexpr bool kPacked = kPk;
   struct Args {
     const T* d;
     const T* u;
@@ -260,7 +346,7 @@ struct FactorMode {
     bool rhs_from_V;
   };
   static constexpr int kStageBytes = 3 * kSlots * (int)sizeof(T);
-  static constexpr int kCacheBytes = 2 * 32 * 2 * (int)sizeof(T) + 2 * 32 * (int)sizeof(T);
+  static constexpr int kCacheBytes = 2 * 32 * 2 * (int)sizeof(T) + 2 * 32 * (int)sizeof(T) + kTabBytes;
   static constexpr int kWarpBytes = 2 * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);  // CTAs per SM that shared memory allows
 
@@ -271,7 +357,13 @@ struct FactorMode {
     T* sd = reinterpret_cast<T*>(buf);
     T* su = sd + kSlots;
     T* sb = su + kSlots;
-    if (visit == 1) {
+    if (kPk) {
+      const long long blk = __shfl_sync(kFull, m.first, 0);
+      const int e = chunk_elems(m, n, lane);
+      stage_block(sd, visit == 1 ? static_cast<const T*>(P.fac) : A.d, blk, e, lane);
+      stage_block(su, A.u, blk, e, lane);
+      stage_block(sb, static_cast<const T*>(A.x), blk, e, lane);
+    } else if (visit == 1) {
       const T* fac = static_cast<const T*>(P.fac);
       for_branch_elements<T>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
         const int q = sidx(lj - 1 - t, jj);
@@ -310,11 +402,12 @@ struct FactorMode {
     T* cslot = reinterpret_cast<T*>(cache);                   // [2][32][2] contributions
     T* cx = cslot + 2 * 32 * 2;                               // [2][32] distal solutions
     T* slot = static_cast<T*>(P.cd);                          // [nb][2]
+    const auto Q = IdxOf<kPk>::make(m, n, lane, cache + kCacheBytes - kTabBytes);
     if (lane >= n) return;
     const int pos = c0 + lane;
     const int len = m.len;
     if (visit == 0) {
-      T D = sd[sidx(0, lane)], B = sb[sidx(0, lane)];
+      T D = sd[Q(0, lane)], B = sb[Q(0, lane)];
       for (int i = 0; i < m.nchild; ++i) {
         const int cp = child_pos(P, m, i);
         const int loc = cp - pv.c0;
@@ -323,27 +416,27 @@ struct FactorMode {
         B -= local ? cslot[(pv.which * 32 + loc) * 2 + 1] : slot_load(slot + 2 * cp + 1, m);
       }
       for (int k = 0; k < len - 1; ++k) {
-        const T uk = su[sidx(k, lane)];
+        const T uk = su[Q(k, lane)];
         const T r = rcp_t(D);
-        sd[sidx(k, lane)] = r;
-        sb[sidx(k, lane)] = B;
+        sd[Q(k, lane)] = r;
+        sb[Q(k, lane)] = B;
         const T f = uk * r;
-        D = sd[sidx(k + 1, lane)] - f * uk;
+        D = sd[Q(k + 1, lane)] - f * uk;
         if (kCable) D -= uk;  // the edge to the chain child
-        B = sb[sidx(k + 1, lane)] - f * B;
+        B = sb[Q(k + 1, lane)] - f * B;
       }
       const int k = len - 1;
       const T r = rcp_t(D);
-      sd[sidx(k, lane)] = r;
+      sd[Q(k, lane)] = r;
       T c0v = T(0), c1v = T(0);
       if (m.pcomp >= 0) {
-        sb[sidx(k, lane)] = B;
-        const T uk = su[sidx(k, lane)];
+        sb[Q(k, lane)] = B;
+        const T uk = su[Q(k, lane)];
         const T f = uk * r;
         c0v = kCable ? f * uk + uk : f * uk;
         c1v = f * B;
       } else {
-        sb[sidx(k, lane)] = B * r;  // solve root
+        sb[Q(k, lane)] = B * r;  // solve root
       }
       slot[2 * pos] = c0v;
       slot[2 * pos + 1] = c1v;
@@ -357,7 +450,7 @@ struct FactorMode {
       xp = (loc >= 0 && loc < pv.n) ? cx[pv.which * 32 + loc] : A.x[m.pcomp];
     }
     for (int k = len - 1; k >= 0; --k) {
-      const int q = sidx(k, lane);
+      const int q = Q(k, lane);
       const T xi = (m.pcomp < 0 && k == len - 1) ? sb[q] : (sb[q] - su[q] * xp) * sd[q];
       sb[q] = xi;
       xp = xi;
@@ -370,6 +463,15 @@ struct FactorMode {
     const T* sd = reinterpret_cast<const T*>(buf);
     const T* sb = sd + 2 * kSlots;
     T* fac = static_cast<T*>(P.fac);
+    if (kPk) {
+      const long long blk = __shfl_sync(kFull, m.first, 0);
+      const int e = chunk_elems(m, n, lane);
+      for (int i = lane; i < e; i += 32) {
+        if (visit == 0) fac[blk + i] = sd[i];
+        A.x[blk + i] = sb[i];
+      }
+      return;
+    }
     for_branch_elements<T>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
       const int q = sidx(lj - 1 - t, jj);
       if (visit == 0) fac[fj + t] = sd[q];
@@ -417,7 +519,7 @@ __device__ void run_task(const DevPlan& P, const typename M::Args& A, int t, int
   unsigned char* cache = wbase + 2 * M::kStageBytes;
   auto buf = [wbase](int which) { return wbase + which * M::kStageBytes; };
   auto meta = [&](const Pos& p) {
-    return load_meta(P, p.c0 + lane, p.visit < ve && lane < p.n, M::kWantDs && p.visit == 1);
+    return load_meta<M::kPacked>(P, p.c0 + lane, p.visit < ve && lane < p.n, M::kWantDs && p.visit == 1);
   };
   Pos cur = pos_level(vb, vb == 0 ? nl - 1 : 0, lp);
   Meta m_cur = meta(cur);
@@ -539,9 +641,13 @@ cudaError_t launch_phases(const DevPlan& P, const typename M::Args& A, int grid,
   return cudaSuccess;
 }
 
-using F64 = FactorMode<double, false>;
-using F32 = FactorMode<float, false>;
-using Cable = FactorMode<double, true>;
+using F64 = FactorMode<double, false, false>;
+using F32 = FactorMode<float, false, false>;
+using Cable = FactorMode<double, true, false>;
+using CompMode = CompModeT<false>;
+using PkF64 = FactorMode<double, false, true>;
+using PkF32 = FactorMode<float, false, true>;
+using PkComp = CompModeT<true>;
 
 }  // namespace
 
@@ -550,6 +656,9 @@ cudaError_t prepare_unit_kernels(DevPlan& P) {
   if (e == cudaSuccess) e = grid_of<F32>(P, &P.grid[1]);
   if (e == cudaSuccess) e = grid_of<Cable>(P, &P.grid[2]);
   if (e == cudaSuccess) e = grid_of<CompMode>(P, &P.grid[3]);
+  if (e == cudaSuccess) e = grid_of<PkF64>(P, &P.grid[4]);
+  if (e == cudaSuccess) e = grid_of<PkF32>(P, &P.grid[5]);
+  if (e == cudaSuccess) e = grid_of<PkComp>(P, &P.grid[6]);
   return e;
 }
 
@@ -573,6 +682,22 @@ cudaError_t launch_unit_solve_compensated(const DevPlan& P, const float* d, cons
                                           cudaStream_t s) {
   CompMode::Args A{d, u, b, x};
   return launch_phases<CompMode>(P, A, P.grid[3], s);
+}
+
+cudaError_t launch_pk_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s) {
+  PkF64::Args A{d, u, nullptr, nullptr, b, 0.0, 0.0, 0.0, false};
+  return launch_phases<PkF64>(P, A, P.grid[4], s);
+}
+
+cudaError_t launch_pk_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s) {
+  PkF32::Args A{d, u, nullptr, nullptr, b, 0.f, 0.f, 0.f, false};
+  return launch_phases<PkF32>(P, A, P.grid[5], s);
+}
+
+cudaError_t launch_pk_solve_compensated(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
+                                        cudaStream_t s) {
+  PkComp::Args A{d, u, b, x};
+  return launch_phases<PkComp>(P, A, P.grid[6], s);
 }
 
 }  // namespace hines

@@ -35,6 +35,7 @@ EXPORTS = [
     "hines_cable_adjoint_step", "hines_cable_loss_seed", "hines_cable_loss_accumulate", "hines_plan_status",
     "hines_status_string",
     "hines_solve_f64_noalloc",
+    "hines_plan_export_packed", "hines_pack", "hines_unpack", "hines_solve_packed", "hines_solve_compensated_packed",
 ]
 
 
@@ -54,7 +55,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("n_cells", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("n_tasks", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("n_unknowns", ctypes.c_int64),
                 ("n_branches", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("metadata_bytes", ctypes.c_int64)]
+                ("metadata_bytes", ctypes.c_int64), ("n_packed", ctypes.c_int64)]
 
 
 def lib():
@@ -83,6 +84,11 @@ def lib():
             L.hines_cable_loss_accumulate.argtypes = [vp, vp, vp, vp, vp]
             L.hines_plan_status.argtypes = [vp, ctypes.POINTER(i32)]
             L.hines_solve_f64_noalloc.argtypes = [ctypes.c_int64, i32, vp, vp, vp, vp, vp, vp]
+            L.hines_plan_export_packed.argtypes = [vp, vp]
+            L.hines_pack.argtypes = [vp, i32, vp, vp, vp]
+            L.hines_unpack.argtypes = [vp, i32, vp, vp, vp]
+            L.hines_solve_packed.argtypes = [vp, i32, vp, vp, vp, vp]
+            L.hines_solve_compensated_packed.argtypes = [vp, vp, vp, vp, vp, vp]
             L.hines_status_string.argtypes = [i32]
             L.hines_status_string.restype = ctypes.c_char_p
             for name in EXPORTS:
@@ -130,6 +136,7 @@ class Plan:
         self.n_tasks = info.n_tasks
         self.workspace_bytes = info.workspace_bytes
         self.metadata_bytes = info.metadata_bytes
+        self.n_packed = info.n_packed
         self.host_only = host_only
         off = np.empty(self.n_cells + 1, np.int64)
         _check(lib().hines_plan_layout(self._h, _np_ptr(off)), "hines_plan_layout")
@@ -151,6 +158,12 @@ class Plan:
         out = {k: np.empty(self.n_branches, np.int64) for k in ("branch_task", "branch_kind", "task_order")}
         _check(lib().hines_plan_export_tasks(self._h, _np_ptr(out["branch_task"]), _np_ptr(out["branch_kind"]),
                                              _np_ptr(out["task_order"])), "hines_plan_export_tasks")
+        return out
+
+    def export_packed(self) -> np.ndarray:
+        """Natural index held by each solver-layout slot (-1: padding)."""
+        out = np.empty(self.n_packed, np.int64)
+        _check(lib().hines_plan_export_packed(self._h, _np_ptr(out)), "hines_plan_export_packed")
         return out
 
     def status(self) -> int:
@@ -215,6 +228,60 @@ def solve_compensated(plan: Plan, d, u, b, x=None):
     _check(lib().hines_solve_compensated(plan.handle, _dptr(d, torch.float32, n, "d"), _dptr(u, torch.float32, n, "u"),
                                          _dptr(b, torch.float32, n, "b"), _dptr(x, torch.float64, n, "x"), _stream()),
            "hines_solve_compensated")
+    return x
+
+
+def _pptr(t, dtype, n, name):
+    """Pointer to a solver-layout tensor (n_packed elements, 16-byte aligned)."""
+    p = _dptr(t, dtype, n, name)
+    if p.value and p.value % 16:
+        raise ValueError(f"{name}: solver-layout arrays must be 16-byte aligned")
+    return p
+
+
+def pack(plan: Plan, natural, packed=None):
+    """Natural-layout tensor (float32 or float64) -> solver layout."""
+    torch = _torch()
+    if packed is None:
+        packed = torch.empty(plan.n_packed, dtype=natural.dtype, device=natural.device)
+    eb = natural.element_size()
+    _check(lib().hines_pack(plan.handle, eb, _dptr(natural, natural.dtype, plan.n_unknowns, "natural"),
+                            _pptr(packed, natural.dtype, plan.n_packed, "packed"), _stream()), "hines_pack")
+    return packed
+
+
+def unpack(plan: Plan, packed, natural=None):
+    """Solver-layout tensor -> natural layout."""
+    torch = _torch()
+    if natural is None:
+        natural = torch.empty(plan.n_unknowns, dtype=packed.dtype, device=packed.device)
+    eb = packed.element_size()
+    _check(lib().hines_unpack(plan.handle, eb, _pptr(packed, packed.dtype, plan.n_packed, "packed"),
+                              _dptr(natural, packed.dtype, plan.n_unknowns, "natural"), _stream()), "hines_unpack")
+    return natural
+
+
+def solve_packed(plan: Plan, d, u, b):
+    """hines_solve on solver-layout tensors (float64 or float32), in place in b."""
+    torch = _torch()
+    dt = b.dtype
+    code = HINES_F64 if dt == torch.float64 else HINES_F32
+    n = plan.n_packed
+    _check(lib().hines_solve_packed(plan.handle, code, _pptr(d, dt, n, "d"), _pptr(u, dt, n, "u"),
+                                    _pptr(b, dt, n, "b"), _stream()), "hines_solve_packed")
+    return b
+
+
+def solve_compensated_packed(plan: Plan, d, u, b, x=None):
+    """hines_solve_compensated on solver-layout tensors; x float64 in the solver layout."""
+    torch = _torch()
+    n = plan.n_packed
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=b.device)
+    _check(lib().hines_solve_compensated_packed(plan.handle, _pptr(d, torch.float32, n, "d"),
+                                                _pptr(u, torch.float32, n, "u"), _pptr(b, torch.float32, n, "b"),
+                                                _pptr(x, torch.float64, n, "x"), _stream()),
+           "hines_solve_compensated_packed")
     return x
 
 

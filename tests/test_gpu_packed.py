@@ -1,0 +1,109 @@
+"""Solver layout (Section 5's per-chunk interleaving) through the C-ABI:
+pack/unpack round trips, and solves on solver-layout arrays, which must give
+bit for bit the results of the natural-layout solves (the arithmetic and its
+order are the same; only where each value lives differs) and match the oracle.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1810_12742_gb300 import hines as H
+from paper_1810_12742_gb300 import inputs as I
+from tests.test_gpu_parity import cell_rel_err, dev, zoo_batch
+
+pytestmark = pytest.mark.gpu
+
+
+def uneven_subset():
+    w = I.WORKLOADS["uneven_mixed"]
+    cls = I.cell_classes(w)
+    cells = np.concatenate([np.nonzero(cls == 0)[0][:40], np.nonzero(cls == 1)[0][:6]])
+    return I.population(w, cells=cells, margin=0.1)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_pack_unpack_round_trip(dtype):
+    ncomp, parent, c = zoo_batch(41)
+    plan = H.Plan(ncomp, parent)
+    a = dev(c["b"], dtype)
+    pk = H.pack(plan, a)
+    assert pk.numel() == plan.n_packed
+    slots = plan.export_packed()
+    ref = np.zeros(plan.n_packed)
+    ref[slots >= 0] = a.cpu().numpy()[slots[slots >= 0]]
+    assert np.array_equal(pk.cpu().numpy(), ref.astype(pk.cpu().numpy().dtype))
+    back = H.unpack(plan, pk)
+    assert torch.equal(back, a)
+
+
+def _natural_and_packed(plan, d, u, b, mode):
+    if mode == "f64":
+        x = b.clone()
+        H.solve(plan, d, u, x)
+        xp = H.pack(plan, b)
+        H.solve_packed(plan, H.pack(plan, d), H.pack(plan, u), xp)
+        return x, H.unpack(plan, xp)
+    if mode == "f32":
+        d, u, b = (t.float() for t in (d, u, b))
+        x = b.clone()
+        H.solve(plan, d, u, x)
+        xp = H.pack(plan, b)
+        H.solve_packed(plan, H.pack(plan, d), H.pack(plan, u), xp)
+        return x, H.unpack(plan, xp)
+    d, u, b = (t.float() for t in (d, u, b))
+    x = H.solve_compensated(plan, d, u, b)
+    xp = H.solve_compensated_packed(plan, H.pack(plan, d), H.pack(plan, u), H.pack(plan, b))
+    return x, H.unpack(plan, xp)
+
+
+@pytest.mark.parametrize("mode", ["f64", "f32", "comp"])
+@pytest.mark.parametrize("split", [False, True])
+def test_packed_solves_equal_natural_zoo(mode, split):
+    ncomp, parent, c = zoo_batch(43)
+    plan = H.Plan(ncomp, parent, split_branches=split)
+    x, xp = _natural_and_packed(plan, dev(c["d"]), dev(c["u"]), dev(c["b"]), mode)
+    assert torch.equal(x, xp)
+    widen = mode != "f64"
+    cast = (lambda a: a.astype(np.float32).astype(np.float64)) if widen else (lambda a: a)
+    ref = oracle.solve_batch(ncomp, parent, cast(c["d"]), cast(c["u"]), cast(c["b"]))
+    tol = {"f64": 1e-12, "f32": 1e-5, "comp": 1e-10}[mode]
+    assert cell_rel_err(xp.double().cpu().numpy(), ref, np.concatenate(([0], np.cumsum(ncomp)))).max() <= tol
+
+
+@pytest.mark.parametrize("mode", ["f64", "f32", "comp"])
+@pytest.mark.parametrize("pack", [0, -1])
+def test_packed_solves_equal_natural_uneven(mode, pack):
+    pop = uneven_subset()
+    plan = H.Plan(pop["ncomp"], pop["parent"], pack_compartments=pack)
+    x, xp = _natural_and_packed(plan, dev(pop["d"]), dev(pop["u"]), dev(pop["b"]), mode)
+    assert torch.equal(x, xp)
+
+
+def test_packed_inputs_not_modified_and_repeatable():
+    ncomp, parent, c = zoo_batch(47)
+    plan = H.Plan(ncomp, parent)
+    d, u, b = (H.pack(plan, dev(c[k], torch.float32)) for k in ("d", "u", "b"))
+    d0, u0, b0 = d.clone(), u.clone(), b.clone()
+    x1 = H.solve_compensated_packed(plan, d, u, b)
+    x2 = H.solve_compensated_packed(plan, d, u, b)
+    assert torch.equal(d, d0) and torch.equal(u, u0) and torch.equal(b, b0)
+    real = torch.as_tensor(plan.export_packed() >= 0, device="cuda")
+    assert torch.equal(x1[real], x2[real])
+
+
+def test_packed_misaligned_rejected():
+    ncomp, parent, c = zoo_batch(49, sizes=(17, 64))
+    plan = H.Plan(ncomp, parent)
+    buf = torch.zeros(plan.n_packed + 1, dtype=torch.float32, device="cuda")
+    d = buf[1:]  # 4-byte offset: not 16-byte aligned
+    ok = H.pack(plan, dev(c["d"], torch.float32))
+    with pytest.raises(ValueError):
+        H.solve_compensated_packed(plan, d, ok, ok)
+    x = torch.empty(plan.n_packed, dtype=torch.float64, device="cuda")
+    vp = ctypes.c_void_p
+    code = H.lib().hines_solve_compensated_packed(plan.handle, vp(d.data_ptr()), vp(ok.data_ptr()),
+                                                  vp(ok.data_ptr()), vp(x.data_ptr()), vp(0))
+    assert code == 1  # HINES_ERR_INVALID_ARG, nothing launched

@@ -212,7 +212,53 @@ def _compare(ncomp, parent, split, sort_by_length=False, pack=0):
         assert np.array_equal(got[k], ref[k]), k
     assert got["len"].max(initial=0) <= CAP
     assert plan.n_unknowns == int(np.sum(ncomp))
+    slots = plan.export_packed()
+    assert plan.n_packed == slots.size
+    assert np.array_equal(slots, py_packed(got))
     return got
+
+
+def py_packed(ex):
+    """Restatement of the solver layout: chunks of at most 32 consecutive
+    positions of one task level; in a chunk's block, row r lists the r-th
+    compartment from the distal end of every branch longer than r, in lane
+    order; blocks padded to multiples of 4 slots."""
+    order, task, ln, par, first = (ex[k] for k in ("task_order", "branch_task", "len", "parent_branch", "first"))
+    nb = order.size
+    rl = np.zeros(nb, np.int64)
+    for b in range(nb):
+        q = b
+        while par[q] >= 0 and task[par[q]] == task[b]:
+            rl[b] += 1
+            q = par[q]
+    slots, pos = [], 0
+    while pos < nb:
+        b0 = order[pos]
+        end = pos
+        while end < nb and end - pos < LANES and task[order[end]] == task[b0] and rl[order[end]] == rl[b0]:
+            end += 1
+        chunk = order[pos:end]
+        e = 0
+        for r in range(CAP):
+            for b in chunk:
+                if ln[b] > r:
+                    slots.append(first[b] + ln[b] - 1 - r)
+                    e += 1
+        slots += [-1] * (-e % 4)
+        pos = end
+    return np.array(slots, np.int64)
+
+
+def test_solver_layout_is_a_permutation():
+    rng = np.random.default_rng(5)
+    trees = list(tree_zoo(rng, 700).values())
+    ncomp = [t.size for t in trees]
+    plan = H.Plan(ncomp, np.concatenate(trees), host_only=True)
+    s = plan.export_packed()
+    real = s[s >= 0]
+    assert np.array_equal(np.sort(real), np.arange(plan.n_unknowns))
+    assert plan.n_packed - plan.n_unknowns == np.count_nonzero(s < 0)
+    assert plan.n_packed % 4 == 0
 
 
 @pytest.mark.parametrize("split", [False, True])
