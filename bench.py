@@ -278,6 +278,16 @@ def main():
     err_ref = max_rel_err(xr, True)
     del xr
 
+    # the same solve on arrays kept in the solver layout (Section 5's per-chunk
+    # interleaving): what a simulation that stores its state in that layout pays
+    pk = {k: H.pack(plan, f32[k]) for k in ("d", "u", "b")}
+    xpk = torch.empty(plan.n_packed, dtype=torch.float64, device="cuda")
+    ms_pk = timed(lambda: H.solve_compensated_packed(plan, pk["d"], pk["u"], pk["b"], xpk), args.steps)
+    err_pk = max_rel_err(H.unpack(plan, xpk), True)
+    ms_pack = timed(lambda: [H.pack(plan, f32[k], pk[k]) for k in ("d", "u", "b")], 3)
+    ms_unpack = timed(lambda: H.unpack(plan, xpk, x), 3)
+    del pk, xpk
+
     # end to end through the public API with pinned host buffers
     host = {k: torch.as_tensor(pop[k].astype(np.float32)).pin_memory() for k in ("d", "u", "b")}
     xh = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -301,6 +311,11 @@ def main():
         "fp64": {"value": n / (ms64 * 1e-3), "unit": "compartments/s", "ms_per_solve": ms64,
                  "max_rel_err": err64, "roofline_frac": BYTES_F64 * n / (ms64 * 1e-3) / 1e9 / peak,
                  "speedup_of_compensated": ms64 / ms_step},
+        "solver_layout": {"value": n / (ms_pk * 1e-3), "unit": "compartments/s", "ms_per_solve": ms_pk,
+                          "max_rel_err": err_pk, "n_packed": plan.n_packed,
+                          "roofline_frac": BYTES_F32_IN * n / (ms_pk * 1e-3) / 1e9 / peak,
+                          "pack_d_u_b_ms": ms_pack, "unpack_x_ms": ms_unpack,
+                          "path": "hines_solve_compensated_packed on d, u, b, x kept in the solver layout"},
         "fp32_refine": {"value": n / (ms_ref * 1e-3), "unit": "compartments/s", "ms_per_solve": ms_ref,
                         "refine_steps": args.refine_steps, "max_rel_err": err_ref,
                         "roofline_frac": BYTES_F32_IN * n / (ms_ref * 1e-3) / 1e9 / peak},

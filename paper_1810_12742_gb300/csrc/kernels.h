@@ -57,7 +57,8 @@ struct DevPlan {
   const int64_t* pk_perm = nullptr;       // [n_packed] natural index of each solver-layout slot, -1 for padding
   int32_t grid[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // persistent grid size per kernel kind
   // workspace
-  void* fac = nullptr;    // n_unknowns * 8 bytes: factor (FP64 / FP32 solves), FP32 working arrays (refine)
+  void* fac = nullptr;    // 8 bytes per natural or solver-layout slot: factor (FP64 / FP32 solves), FP32 working
+                          // arrays (refine)
   void* cd = nullptr;     // n_branches * 16 bytes: child-to-parent contribution (or root solution) per position
   void* cb = nullptr;     // n_branches * 8 bytes: FP32/FP64 per-branch contribution (CTA-per-cell kernels)
   void* dstate = nullptr; // n_branches * 16 bytes: folded distal state per position (compensated)
