@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <queue>
 
 #include "../../include/hines.h"
 
@@ -358,6 +359,7 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
       for (size_t l = 0; l < ucnt.size(); ++l) cnt[l] += ucnt[l];
     }
     std::vector<int32_t> ids;
+    std::vector<int32_t> pend((size_t)nb, 0);
     for (const auto& g : groups) {
       const int32_t t = P.n_tasks++;
       int32_t nl = 0;
@@ -368,23 +370,54 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
         size += units[(size_t)u].size;
         ids.insert(ids.end(), unit_br[(size_t)u].begin(), unit_br[(size_t)u].end());
       }
-      std::stable_sort(ids.begin(), ids.end(), [&](int32_t x, int32_t y) {
+      // chunks by Hu's list schedule for in-forests: a branch is ready once
+      // all its children in the task sit in earlier chunks; each chunk takes
+      // the (at most 32) ready branches farthest from their unit's root,
+      // ties by length (with sort_by_length), cell, branch.  This needs the
+      // fewest chunks for the task's dependency forest; levels of the kernel
+      // are these chunks, stored root-side first.
+      for (int32_t b : ids) P.br_task[(size_t)b] = t;
+      auto later = [&](int32_t x, int32_t y) {  // priority-queue order: true if x goes after y
         if (P.br_rlevel[(size_t)x] != P.br_rlevel[(size_t)y]) return P.br_rlevel[(size_t)x] < P.br_rlevel[(size_t)y];
         if (sort_by_length && P.br_len[(size_t)x] != P.br_len[(size_t)y])
-          return P.br_len[(size_t)x] > P.br_len[(size_t)y];
-        if (P.br_cell[(size_t)x] != P.br_cell[(size_t)y]) return P.br_cell[(size_t)x] < P.br_cell[(size_t)y];
-        return x < y;
-      });
+          return P.br_len[(size_t)x] < P.br_len[(size_t)y];
+        if (P.br_cell[(size_t)x] != P.br_cell[(size_t)y]) return P.br_cell[(size_t)x] > P.br_cell[(size_t)y];
+        return x > y;
+      };
+      std::priority_queue<int32_t, std::vector<int32_t>, decltype(later)> ready(later);
+      for (int32_t b : ids) {
+        int32_t k = 0;
+        for (int32_t q = P.child_ptr[(size_t)b]; q < P.child_ptr[(size_t)b + 1]; ++q)
+          if (P.br_task[(size_t)P.child[(size_t)q]] == t) ++k;
+        pend[(size_t)b] = k;
+        if (k == 0) ready.push(b);
+      }
+      std::vector<std::vector<int32_t>> chunks;
+      std::vector<int32_t> done;
+      while (!ready.empty()) {
+        chunks.emplace_back();
+        while (!ready.empty() && (int)chunks.back().size() < kLanes) {
+          chunks.back().push_back(ready.top());
+          ready.pop();
+        }
+        for (int32_t b : chunks.back()) {
+          const int32_t pb = P.br_parent[(size_t)b];
+          if (pb >= 0 && P.br_task[(size_t)pb] == t && --pend[(size_t)pb] == 0) done.push_back(pb);
+        }
+        for (int32_t b : done) ready.push(b);
+        done.clear();
+      }
+      nl = (int32_t)chunks.size();
+      ids.clear();
       P.task_kind.push_back(kind);
       P.task_nlvl.push_back(nl);
       P.task_lvl_off.push_back((int64_t)P.tlvl_ptr.size());
       const int32_t base = (int32_t)P.torder.size();
-      size_t k = 0;
-      for (int32_t l = 0; l <= nl; ++l) {
-        while (k < ids.size() && P.br_rlevel[(size_t)ids[k]] < l) ++k;
-        P.tlvl_ptr.push_back(base + (int32_t)k);
+      for (int32_t l = nl - 1; l >= 0; --l) {
+        P.tlvl_ptr.push_back(base + (int32_t)ids.size());
+        ids.insert(ids.end(), chunks[(size_t)l].begin(), chunks[(size_t)l].end());
       }
-      for (int32_t b : ids) P.br_task[(size_t)b] = t;
+      P.tlvl_ptr.push_back(base + (int32_t)ids.size());
       P.torder.insert(P.torder.end(), ids.begin(), ids.end());
       task_size.push_back(size);
     }

@@ -1,6 +1,8 @@
 """Host planner: an independent Python statement of the decomposition,
 splitting and ordering rules must agree bit for bit with the C++ planner
 (host-only plans, no GPU needed)."""
+import heapq
+
 import numpy as np
 import pytest
 
@@ -150,9 +152,37 @@ def py_tasks(ncomp, units, sort_by_length, pack=16384):
             cnt = [(cnt[l] if l < len(cnt) else 0) + (cc[l] if l < len(cc) else 0) for l in range(max(len(cnt), len(cc)))]
         for g in groups:
             ids = [b for u in g for b in u[3]]
-            ids.sort(key=lambda b: (rl[b], -G["len"][b] if sort_by_length else 0, G["cell"][b], b))
-            tasks.append((kind, ids))
+            tasks.append((kind, py_hu(ids, rl, sort_by_length)))
     return tasks
+
+
+def py_hu(ids, rl, sort_by_length):
+    """Hu's list schedule of a task's dependency forest: chunks of at most 32
+    ready branches (all children in the task in earlier chunks), farthest from
+    the unit root first; positions list the chunks root-side first."""
+    inset = set(ids)
+    pend = dict.fromkeys(ids, 0)
+    for b in ids:
+        if G["parent"][b] in inset:
+            pend[G["parent"][b]] += 1
+
+    def key(b):
+        return (-rl[b], -G["len"][b] if sort_by_length else 0, G["cell"][b], b)
+
+    heap = [key(b) for b in ids if pend[b] == 0]
+    heapq.heapify(heap)
+    chunks = []
+    while heap:
+        ch = [heapq.heappop(heap)[-1] for _ in range(min(LANES, len(heap)))]
+        chunks.append(ch)
+        for b in ch:
+            p = G["parent"][b]
+            if p in inset:
+                pend[p] -= 1
+                if pend[p] == 0:
+                    heapq.heappush(heap, key(p))
+    G.setdefault("chunks", []).extend(list(reversed(chunks)))
+    return [b for ch in reversed(chunks) for b in ch]
 
 
 G = {}
@@ -180,7 +210,7 @@ def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=16384):
     out = {k: np.array(v, np.int64) for k, v in
            dict(first=first, len=length, parent_branch=pbr, level=level, cell=cell, order=order).items()}
     G.clear()
-    G.update(len=length, parent=pbr, level=level, cell=cell)
+    G.update(len=length, parent=pbr, level=level, cell=cell, chunks=[])
     base_of = np.concatenate(([0], np.cumsum([len(bs) for bs in cells]))).astype(np.int64)
     cells_flat = [list(range(base_of[c], base_of[c + 1])) for c in range(len(cells))]
     units = py_units(list(ncomp), cells_flat)
@@ -219,25 +249,13 @@ def _compare(ncomp, parent, split, sort_by_length=False, pack=0):
 
 
 def py_packed(ex):
-    """Restatement of the solver layout: chunks of at most 32 consecutive
-    positions of one task level; in a chunk's block, row r lists the r-th
+    """Restatement of the solver layout: one block per chunk of the schedule
+    (chunks in position order); in a chunk's block, row r lists the r-th
     compartment from the distal end of every branch longer than r, in lane
     order; blocks padded to multiples of 4 slots."""
-    order, task, ln, par, first = (ex[k] for k in ("task_order", "branch_task", "len", "parent_branch", "first"))
-    nb = order.size
-    rl = np.zeros(nb, np.int64)
-    for b in range(nb):
-        q = b
-        while par[q] >= 0 and task[par[q]] == task[b]:
-            rl[b] += 1
-            q = par[q]
-    slots, pos = [], 0
-    while pos < nb:
-        b0 = order[pos]
-        end = pos
-        while end < nb and end - pos < LANES and task[order[end]] == task[b0] and rl[order[end]] == rl[b0]:
-            end += 1
-        chunk = order[pos:end]
+    ln, first = ex["len"], ex["first"]
+    slots = []
+    for chunk in G["chunks"]:
         e = 0
         for r in range(CAP):
             for b in chunk:
@@ -245,7 +263,6 @@ def py_packed(ex):
                     slots.append(first[b] + ln[b] - 1 - r)
                     e += 1
         slots += [-1] * (-e % 4)
-        pos = end
     return np.array(slots, np.int64)
 
 
