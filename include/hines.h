@@ -71,7 +71,7 @@ typedef struct {
                               Section 4, Fig. 4.1); 0: by memory order, so that a chunk of 32
                               branches of a breadth-first numbered cell is one contiguous range */
   int32_t pack_compartments; /* warp tasks are filled with units up to this many compartments
-                                (0: 16384); -1: Section 4's rule instead (a unit joins a task
+                                (0: 24576); -1: Section 4's rule instead (a unit joins a task
                                 while every level of the task holds at most 32 branches) */
   int32_t reserved[3];     /* must be zero */
 } hines_plan_opts;

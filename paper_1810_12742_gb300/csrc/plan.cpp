@@ -309,7 +309,7 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
   // while every relative level holds at most kLanes branches (Section 4's
   // rule with the 32 lanes of a warp)
   const bool lane_rule = pack_compartments < 0;
-  const int64_t pack_max = pack_compartments > 0 ? pack_compartments : 16384;
+  const int64_t pack_max = pack_compartments > 0 ? pack_compartments : kTaskCompartments;
   P.n_tasks = 0;
   P.task_kind.clear();
   P.task_nlvl.clear();

@@ -71,6 +71,7 @@ constexpr int kBranchCap = 16;   // maximum compartments per branch after cappin
 constexpr int kWarpsPerCta = 4;  // warps per CTA of the task kernels (each warp runs its own task)
 constexpr int64_t kUnitMax = 4096;  // largest unit (compartments); larger cells are cut
 constexpr int64_t kPackAlign = 4;   // solver-layout blocks start on multiples of 4 compartments
+constexpr int64_t kTaskCompartments = 24576;  // default fill of a warp task
 
 // Return codes follow hines_status.
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,

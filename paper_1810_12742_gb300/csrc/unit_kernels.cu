@@ -87,15 +87,18 @@ struct Prev {
   int c0, n, which;  // n = 0: none
 };
 
-// Per-branch copy of up to two branches per step (branches are at most 16 long).
-template <typename T, typename F>
+// Per-element work over a chunk's branches in the natural layout: sixteen
+// lanes per branch, two branches per step (branches are at most 16 long), so a
+// step's copies read two contiguous runs.  kPc: also pass the branch's parent
+// compartment.
+template <bool kPc = false, typename F>
 __device__ __forceinline__ void for_branch_elements(const Meta& m, int n, int lane, F&& f) {
   const int half = lane >> 4, t = lane & 15;
   for (int j = 0; j < n; j += 2) {
     const int jj = j + half;
     const long long fj = __shfl_sync(kFull, m.first, jj & 31);
     const int lj = __shfl_sync(kFull, m.len, jj & 31);
-    const long long pc = __shfl_sync(kFull, m.pcomp, jj & 31);
+    const long long pc = kPc ? __shfl_sync(kFull, m.pcomp, jj & 31) : -1;
     if (jj < n && t < lj) f(jj, t, lj, fj, pc);
   }
 }
@@ -195,7 +198,7 @@ struct CompModeT {
       stage_block(su, A.u, blk, e, lane);
       stage_block(sb, A.b, blk, e, lane);
     } else {
-      for_branch_elements<float>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+      for_branch_elements(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
         const int q = sidx(lj - 1 - t, jj);
         cp_async4(&sd[q], A.d + fj + t);
         cp_async4(&su[q], A.u + fj + t);
@@ -317,7 +320,7 @@ struct CompModeT {
       for (int i = lane; i < e; i += 32) A.x[blk + i] = __hiloint2double(__float_as_int(sb[i]), __float_as_int(sd[i]));
       return;
     }
-    for_branch_elements<float>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+    for_branch_elements(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
       const int q = sidx(lj - 1 - t, jj);
       A.x[fj + t] = __hiloint2double(__float_as_int(sb[q]), __float_as_int(sd[q]));
     });
@@ -365,21 +368,21 @@ struct FactorMode {
       stage_block(sb, static_cast<const T*>(A.x), blk, e, lane);
     } else if (visit == 1) {
       const T* fac = static_cast<const T*>(P.fac);
-      for_branch_elements<T>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+      for_branch_elements(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
         const int q = sidx(lj - 1 - t, jj);
         cp_async(&sd[q], fac + fj + t);
         cp_async(&su[q], A.u + fj + t);
         cp_async(&sb[q], A.x + fj + t);
       });
     } else if (!kCable) {
-      for_branch_elements<T>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+      for_branch_elements(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
         const int q = sidx(lj - 1 - t, jj);
         cp_async(&sd[q], A.d + fj + t);
         cp_async(&su[q], A.u + fj + t);
         cp_async(&sb[q], A.x + fj + t);
       });
     } else {
-      for_branch_elements<T>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long pc) {
+      for_branch_elements<true>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long pc) {
         const long long i = fj + t;
         const T si = A.s[i], gi = A.g[i], ui = A.u[i], vi = A.x[i];
         T dd = si * (T(1) + A.theta * A.dt * gi);
@@ -472,7 +475,7 @@ struct FactorMode {
       }
       return;
     }
-    for_branch_elements<T>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+    for_branch_elements(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
       const int q = sidx(lj - 1 - t, jj);
       if (visit == 0) fac[fj + t] = sd[q];
       A.x[fj + t] = sb[q];

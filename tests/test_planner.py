@@ -121,7 +121,7 @@ def py_units(ncomp, cells_flat):
     return units
 
 
-def py_tasks(ncomp, units, sort_by_length, pack=16384):
+def py_tasks(ncomp, units, sort_by_length, pack=24576):
     rl = {}
     for kind, c, root, ids in units:
         for b in ids:
@@ -188,7 +188,7 @@ def py_hu(ids, rl, sort_by_length):
 G = {}
 
 
-def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=16384):
+def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=24576):
     off = np.concatenate(([0], np.cumsum(ncomp))).astype(np.int64)
     cells = [py_branches(parent[off[c]:off[c + 1]]) for c in range(len(ncomp))]
     if split:
@@ -236,7 +236,7 @@ def _compare(ncomp, parent, split, sort_by_length=False, pack=0):
                   pack_compartments=pack)
     got = plan.export()
     got.update(plan.export_tasks())
-    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split, sort_by_length, pack if pack else 16384)
+    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split, sort_by_length, pack if pack else 24576)
     assert plan.n_tasks == ref.pop("n_tasks")
     for k in ref:
         assert np.array_equal(got[k], ref[k]), k
