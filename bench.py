@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--refine-reps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["headline", "solver_layout"],
+                    help="run only this solve, warmup + steps times, and print its time (small profiling runs)")
     return ap.parse_args()
 
 
@@ -202,6 +204,27 @@ def main():
 
     def step():
         H.solve_compensated(plan, f32["d"], f32["u"], f32["b"], x)
+
+    if args.only:
+        if args.only == "solver_layout":
+            pk = {k: H.pack(plan, f32[k]) for k in ("d", "u", "b")}
+            xpk = torch.empty(plan.n_packed, dtype=torch.float64, device="cuda")
+
+            def step():  # noqa: F811
+                H.solve_compensated_packed(plan, pk["d"], pk["u"], pk["b"], xpk)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"only": args.only, "compartments": n, "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                              "status": plan.status()}), flush=True)
+        return
 
     for _ in range(args.warmup):
         step()
