@@ -254,6 +254,17 @@ hines_status hines_cable_solve(hines_plan_t plan, const double *s, const double 
                                double *rhs_inout, double dt, int32_t theta, hines_stream_t stream);
 
 /*
+ * hines_cable_step and hines_cable_solve on solver-layout arrays (n_packed
+ * elements each, 16-byte aligned; padding slots ignored), so that a rollout
+ * keeps s, g, u and V in the solver layout from the first step to the last.
+ * Same arithmetic, bit for bit, as the natural-layout calls.
+ */
+hines_status hines_cable_step_packed(hines_plan_t plan, const double *s, const double *g, const double *u,
+                                     double *V_inout, double dt, double E, int32_t theta, hines_stream_t stream);
+hines_status hines_cable_solve_packed(hines_plan_t plan, const double *s, const double *g, const double *u,
+                                      double *rhs_inout, double dt, int32_t theta, hines_stream_t stream);
+
+/*
  * Adjoint gather for x = A^{-1} b with lambda = A^{-1} xbar (A symmetric, so
  * lambda is a second Hines solve):
  *   grad_d[i] = -lambda_i x_i

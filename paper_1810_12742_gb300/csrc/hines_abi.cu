@@ -370,6 +370,26 @@ hines_status hines_cable_solve(hines_plan_t p, const double* s, const double* g,
                                            reinterpret_cast<cudaStream_t>(stream)));
 }
 
+hines_status hines_cable_step_packed(hines_plan_t p, const double* s, const double* g, const double* u,
+                                     double* V_inout, double dt, double E, int32_t theta, hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need_pk(p, s) || !need_pk(p, g) || !need_pk(p, u) || !need_pk(p, V_inout)) return HINES_ERR_INVALID_ARG;
+  if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
+  return launched(hines::launch_pk_cable(p->dev, s, g, u, V_inout, dt, E, theta, true,
+                                         reinterpret_cast<cudaStream_t>(stream)));
+}
+
+hines_status hines_cable_solve_packed(hines_plan_t p, const double* s, const double* g, const double* u,
+                                      double* rhs_inout, double dt, int32_t theta, hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (!need_pk(p, s) || !need_pk(p, g) || !need_pk(p, u) || !need_pk(p, rhs_inout)) return HINES_ERR_INVALID_ARG;
+  if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
+  return launched(hines::launch_pk_cable(p->dev, s, g, u, rhs_inout, dt, 0.0, theta, false,
+                                         reinterpret_cast<cudaStream_t>(stream)));
+}
+
 hines_status hines_grad_du(hines_plan_t p, const double* lambda, const double* x, double* grad_d, double* grad_u,
                            hines_stream_t stream) {
   hines_status st = check_plan(p);

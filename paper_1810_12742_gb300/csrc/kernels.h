@@ -81,6 +81,8 @@ cudaError_t launch_pk_solve_f64(const DevPlan& P, const double* d, const double*
 cudaError_t launch_pk_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s);
 cudaError_t launch_pk_solve_compensated(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
                                         cudaStream_t s);
+cudaError_t launch_pk_cable(const DevPlan& P, const double* sv, const double* g, const double* u, double* V, double dt,
+                            double E, int theta, bool rhs_from_V, cudaStream_t s);
 // Natural <-> solver layout permutations (elem_bytes 4 or 8).
 cudaError_t launch_pack(const DevPlan& P, int elem_bytes, const void* natural, void* packed, cudaStream_t s);
 cudaError_t launch_unpack(const DevPlan& P, int elem_bytes, const void* packed, void* natural, cudaStream_t s);

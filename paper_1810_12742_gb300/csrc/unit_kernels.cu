@@ -337,7 +337,6 @@ struct CompModeT {
 // ============================================================================
 template <typename T, bool kCable, bool kPk>
 struct FactorMode {
-  static_assert(!(kCable && kPk), "the cable rebuild runs in the natural layout");
   static constexpr bool kPacked = kPk;
   struct Args {
     const T* d;
@@ -360,7 +359,19 @@ struct FactorMode {
     T* sd = reinterpret_cast<T*>(buf);
     T* su = sd + kSlots;
     T* sb = su + kSlots;
-    if (kPk) {
+    if (kPk && kCable && visit == 0) {
+      // the block's rows in place; the own edge to the parent is taken off
+      // the diagonal in compute(), where the cell's root compartment is known
+      const long long blk = __shfl_sync(kFull, m.first, 0);
+      const int e = chunk_elems(m, n, lane);
+      for (int i = lane; i < e; i += 32) {
+        const long long g = blk + i;
+        const T si = A.s[g], gi = A.g[g], ui = A.u[g], vi = A.x[g];
+        sd[i] = si * (T(1) + A.theta * A.dt * gi);
+        su[i] = ui;
+        sb[i] = A.rhs_from_V ? si * vi + si * A.dt * gi * (A.E - (T(1) - A.theta) * vi) : vi;
+      }
+    } else if (kPk) {
       const long long blk = __shfl_sync(kFull, m.first, 0);
       const int e = chunk_elems(m, n, lane);
       stage_block(sd, visit == 1 ? static_cast<const T*>(P.fac) : A.d, blk, e, lane);
@@ -410,6 +421,10 @@ struct FactorMode {
     const int pos = c0 + lane;
     const int len = m.len;
     if (visit == 0) {
+      if (kPk && kCable) {  // own edge to the parent, except at the cell's root compartment
+        for (int k = 0; k < len; ++k)
+          if (!(m.pcomp < 0 && k == len - 1)) sd[Q(k, lane)] -= su[Q(k, lane)];
+      }
       T D = sd[Q(0, lane)], B = sb[Q(0, lane)];
       for (int i = 0; i < m.nchild; ++i) {
         const int cp = child_pos(P, m, i);
@@ -651,6 +666,7 @@ using CompMode = CompModeT<false>;
 using PkF64 = FactorMode<double, false, true>;
 using PkF32 = FactorMode<float, false, true>;
 using PkComp = CompModeT<true>;
+using PkCable = FactorMode<double, true, true>;
 
 }  // namespace
 
@@ -662,6 +678,7 @@ cudaError_t prepare_unit_kernels(DevPlan& P) {
   if (e == cudaSuccess) e = grid_of<PkF64>(P, &P.grid[4]);
   if (e == cudaSuccess) e = grid_of<PkF32>(P, &P.grid[5]);
   if (e == cudaSuccess) e = grid_of<PkComp>(P, &P.grid[6]);
+  if (e == cudaSuccess) e = grid_of<PkCable>(P, &P.grid[7]);
   return e;
 }
 
@@ -701,6 +718,12 @@ cudaError_t launch_pk_solve_compensated(const DevPlan& P, const float* d, const 
                                         cudaStream_t s) {
   PkComp::Args A{d, u, b, x};
   return launch_phases<PkComp>(P, A, P.grid[6], s);
+}
+
+cudaError_t launch_pk_cable(const DevPlan& P, const double* sv, const double* g, const double* u, double* V, double dt,
+                            double E, int theta, bool rhs_from_V, cudaStream_t s) {
+  PkCable::Args A{nullptr, u, sv, g, V, dt, E, (double)theta, rhs_from_V};
+  return launch_phases<PkCable>(P, A, P.grid[7], s);
 }
 
 }  // namespace hines

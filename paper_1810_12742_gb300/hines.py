@@ -36,6 +36,7 @@ EXPORTS = [
     "hines_status_string",
     "hines_solve_f64_noalloc",
     "hines_plan_export_packed", "hines_pack", "hines_unpack", "hines_solve_packed", "hines_solve_compensated_packed",
+    "hines_cable_step_packed", "hines_cable_solve_packed",
 ]
 
 
@@ -89,6 +90,8 @@ def lib():
             L.hines_unpack.argtypes = [vp, i32, vp, vp, vp]
             L.hines_solve_packed.argtypes = [vp, i32, vp, vp, vp, vp]
             L.hines_solve_compensated_packed.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.hines_cable_step_packed.argtypes = [vp, vp, vp, vp, vp, f64, f64, i32, vp]
+            L.hines_cable_solve_packed.argtypes = [vp, vp, vp, vp, vp, f64, i32, vp]
             L.hines_status_string.argtypes = [i32]
             L.hines_status_string.restype = ctypes.c_char_p
             for name in EXPORTS:
@@ -283,6 +286,26 @@ def solve_compensated_packed(plan: Plan, d, u, b, x=None):
                                                 _pptr(x, torch.float64, n, "x"), _stream()),
            "hines_solve_compensated_packed")
     return x
+
+
+def cable_step_packed(plan: Plan, s, g, u, V, dt: float, E: float, theta: int = 1):
+    """hines_cable_step on solver-layout float64 tensors (V in place)."""
+    torch = _torch()
+    n = plan.n_packed
+    _check(lib().hines_cable_step_packed(plan.handle, _pptr(s, torch.float64, n, "s"), _pptr(g, torch.float64, n, "g"),
+                                         _pptr(u, torch.float64, n, "u"), _pptr(V, torch.float64, n, "V"),
+                                         float(dt), float(E), int(theta), _stream()), "hines_cable_step_packed")
+    return V
+
+
+def cable_solve_packed(plan: Plan, s, g, u, y, dt: float, theta: int = 1):
+    """hines_cable_solve on solver-layout float64 tensors (y in place)."""
+    torch = _torch()
+    n = plan.n_packed
+    _check(lib().hines_cable_solve_packed(plan.handle, _pptr(s, torch.float64, n, "s"), _pptr(g, torch.float64, n, "g"),
+                                          _pptr(u, torch.float64, n, "u"), _pptr(y, torch.float64, n, "y"),
+                                          float(dt), int(theta), _stream()), "hines_cable_solve_packed")
+    return y
 
 
 def solve_refine(plan: Plan, d, u, b, x=None, steps: int = 2, relres=None):

@@ -22,22 +22,45 @@ from . import hines as H
 
 class CableStepper:
     """``steps`` implicit-Euler steps of the passive cable, captured in one CUDA
-    graph; ``replay()`` advances V in place by ``steps`` steps."""
+    graph; ``replay()`` advances the state by ``steps`` steps.
 
-    def __init__(self, plan: H.Plan, s, g, u, V, dt: float, E: float, theta: int = 1, steps: int = 1000):
-        self.plan, self.args = plan, (s, g, u, V, dt, E, theta)
+    layout "natural": the graph steps the caller's V in place.  layout
+    "solver": s, g, u and V are permuted once into the solver layout
+    (Section 5) and the graph steps that copy; ``fetch()`` writes the state
+    back into the caller's V."""
+
+    def __init__(self, plan: H.Plan, s, g, u, V, dt: float, E: float, theta: int = 1, steps: int = 1000,
+                 layout: str = "natural"):
+        if layout not in ("natural", "solver"):
+            raise ValueError(f"layout: expected 'natural' or 'solver', got {layout!r}")
+        self.plan, self.V, self.layout = plan, V, layout
         self.steps = steps
+        if layout == "solver":
+            self.pk = [H.pack(plan, t) for t in (s, g, u, V)]
+
+            def step(Vt):
+                H.cable_step_packed(plan, self.pk[0], self.pk[1], self.pk[2], Vt, dt, E, theta)
+            state = self.pk[3]
+        else:
+            def step(Vt):
+                H.cable_step(plan, s, g, u, Vt, dt, E, theta)
+            state = V
         # one eager step on a scratch copy creates the kernels' resources before capture
-        tmp = V.clone()
-        H.cable_step(plan, s, g, u, tmp, dt, E, theta)
+        step(state.clone())
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
             for _ in range(steps):
-                H.cable_step(plan, s, g, u, V, dt, E, theta)
+                step(state)
 
     def replay(self):
         self.graph.replay()
+
+    def fetch(self):
+        """The current state in the caller's V (natural layout)."""
+        if self.layout == "solver":
+            H.unpack(self.plan, self.pk[3], self.V)
+        return self.V
 
 
 def cable_rollout(plan: H.Plan, s, g, u, V0, target, steps: int, dt: float, E: float, theta: int = 1,

@@ -65,6 +65,32 @@ def test_thousand_steps_uneven_subset():
     assert rel_cells(V.cpu().numpy(), ref, plan.offsets) <= 1e-12
 
 
+@pytest.mark.parametrize("theta", [0, 1])
+def test_solver_layout_steps_equal_natural(theta):
+    """hines_cable_step_packed / hines_cable_solve_packed give the natural-layout
+    results bit for bit; the graph stepper in the solver layout too."""
+    w, pop = uneven_subset(24, 2)
+    plan = H.Plan(pop["ncomp"], pop["parent"])
+    s, g, u = dev(pop["s"]), dev(pop["g"]), dev(pop["u"])
+    V = dev(pop["V0"])
+    pk = [H.pack(plan, t) for t in (s, g, u, V)]
+    for _ in range(5):
+        H.cable_step(plan, s, g, u, V, w.dt, w.E, theta)
+        H.cable_step_packed(plan, pk[0], pk[1], pk[2], pk[3], w.dt, w.E, theta)
+    assert torch.equal(H.unpack(plan, pk[3]), V)
+    y = V.clone()
+    yp = H.pack(plan, y)
+    H.cable_solve(plan, s, g, u, y, w.dt, theta)
+    H.cable_solve_packed(plan, pk[0], pk[1], pk[2], yp, w.dt, theta)
+    assert torch.equal(H.unpack(plan, yp), y)
+    V1, V2 = dev(pop["V0"]), dev(pop["V0"])
+    a = R.CableStepper(plan, s, g, u, V1, w.dt, w.E, theta, steps=7)
+    b = R.CableStepper(plan, s, g, u, V2, w.dt, w.E, theta, steps=7, layout="solver")
+    a.replay()
+    b.replay()
+    assert torch.equal(b.fetch(), V1)
+
+
 def _adjoint_case(cells, steps, ce, theta=1):
     w = I.WORKLOADS["adjoint"]
     pop = I.population(w, cells=cells, keys=("s", "a", "u", "g", "V0", "target"))
