@@ -34,6 +34,8 @@ sys.path.insert(0, ROOT)
 #   FP64:                       read d, u, b in FP64 (24 B) + write x in FP64 (8 B)
 BYTES_F32_IN = 20
 BYTES_F64 = 32
+#   passive-cable step: read s, g, u, V (32 B) + write V (8 B), FP64
+BYTES_CABLE = 40
 
 
 def parse():
@@ -50,6 +52,8 @@ def parse():
     ap.add_argument("--refine-reps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cable-steps", type=int, default=100,
+                    help="passive-cable steps per captured graph for the time-stepping figure (0: skip)")
     ap.add_argument("--only", choices=["headline", "solver_layout"],
                     help="run only this solve, warmup + steps times, and print its time (small profiling runs)")
     return ap.parse_args()
@@ -311,6 +315,39 @@ def main():
     ms_unpack = timed(lambda: H.unpack(plan, xpk, x), 3)
     del pk, xpk
 
+    # passive-cable time stepping (rebuild of d and b from V fused with the FP64
+    # solve), the same trees: K steps captured in one CUDA graph, natural layout
+    # and solver layout
+    cable = None
+    if args.cable_steps > 0:
+        from paper_1810_12742_gb300 import rollout as R
+        ws = I.WORKLOADS["uneven_steps"]
+        cp = I.population(ws, cells=cells, keys=("s", "a", "u", "g", "V0"))
+        cs = {k: torch.as_tensor(cp[k]).cuda() for k in ("s", "g", "u", "V0")}
+        cable = {"steps_per_graph": args.cable_steps, "algorithmic_bytes_per_compartment": BYTES_CABLE,
+                 "path": "hines_cable_step (theta 1) x steps in one CUDA graph"}
+        for layout in ("natural", "solver"):
+            V = cs["V0"].clone()
+            st = R.CableStepper(plan, cs["s"], cs["g"], cs["u"], V, ws.dt, ws.E, 1, steps=args.cable_steps,
+                                layout=layout)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            st.replay()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms = max_over_ranks(a0.elapsed_time(a1) / args.cable_steps)
+            Vn = st.fetch().cpu().numpy()
+            err_c = 0.0
+            for c in sample[:16]:
+                sl = slice(off[c], off[c + 1])
+                ref, _ = oracle.steps_batch(pop["ncomp"][c:c + 1], pop["parent"][sl], cp["s"][sl], cp["g"][sl],
+                                            cp["a"][sl], cp["V0"][sl], args.cable_steps, ws.dt, ws.E, 1)
+                err_c = max(err_c, float(np.abs(Vn[sl] - ref).max() / np.abs(ref).max()))
+            cable[layout] = {"ms_per_step": ms, "compartments_per_s": n / (ms * 1e-3), "max_rel_err": err_c,
+                             "hbm_frac": BYTES_CABLE * n / (ms * 1e-3) / 1e9 / load_peaks()[0]}
+            del st, V
+        del cs, cp
+
     # end to end through the public API with pinned host buffers
     host = {k: torch.as_tensor(pop[k].astype(np.float32)).pin_memory() for k in ("d", "u", "b")}
     xh = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -339,6 +376,7 @@ def main():
                           "roofline_frac": BYTES_F32_IN * n / (ms_pk * 1e-3) / 1e9 / peak,
                           "pack_d_u_b_ms": ms_pack, "unpack_x_ms": ms_unpack,
                           "path": "hines_solve_compensated_packed on d, u, b, x kept in the solver layout"},
+        "cable_steps": cable,
         "fp32_refine": {"value": n / (ms_ref * 1e-3), "unit": "compartments/s", "ms_per_solve": ms_ref,
                         "refine_steps": args.refine_steps, "max_rel_err": err_ref,
                         "roofline_frac": BYTES_F32_IN * n / (ms_ref * 1e-3) / 1e9 / peak},

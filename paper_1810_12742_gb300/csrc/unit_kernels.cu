@@ -354,6 +354,15 @@ struct FactorMode {
 
   static constexpr bool kWantDs = false;
 
+  // Section 1's implicit-Euler system: the membrane part of the diagonal,
+  // s (1 + theta dt g), and the right-hand side s (V + dt g (E - (1 - theta) V)),
+  // each in the fewest operations (theta = 1: s (V + dt E g))
+  __device__ static T cable_diag(const Args& A, T si, T gi) { return si * fma(A.theta * A.dt, gi, T(1)); }
+  __device__ static T cable_rhs(const Args& A, T si, T gi, T vi) {
+    if (A.theta == T(1)) return si * fma(A.dt * A.E, gi, vi);
+    return si * fma(A.dt * gi, fma(A.theta - T(1), vi, A.E), vi);
+  }
+
   __device__ static void stage(const DevPlan& P, const Args& A, int visit, const Meta& m, int n, int lane,
                                unsigned char* buf) {
     T* sd = reinterpret_cast<T*>(buf);
@@ -367,9 +376,9 @@ struct FactorMode {
       for (int i = lane; i < e; i += 32) {
         const long long g = blk + i;
         const T si = A.s[g], gi = A.g[g], ui = A.u[g], vi = A.x[g];
-        sd[i] = si * (T(1) + A.theta * A.dt * gi);
+        sd[i] = cable_diag(A, si, gi);
         su[i] = ui;
-        sb[i] = A.rhs_from_V ? si * vi + si * A.dt * gi * (A.E - (T(1) - A.theta) * vi) : vi;
+        sb[i] = A.rhs_from_V ? cable_rhs(A, si, gi, vi) : vi;
       }
     } else if (kPk) {
       const long long blk = __shfl_sync(kFull, m.first, 0);
@@ -396,9 +405,9 @@ struct FactorMode {
       for_branch_elements<true>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long pc) {
         const long long i = fj + t;
         const T si = A.s[i], gi = A.g[i], ui = A.u[i], vi = A.x[i];
-        T dd = si * (T(1) + A.theta * A.dt * gi);
+        T dd = cable_diag(A, si, gi);
         if (!(pc < 0 && t == 0)) dd -= ui;  // own edge to the parent
-        const T bb = A.rhs_from_V ? si * vi + si * A.dt * gi * (A.E - (T(1) - A.theta) * vi) : vi;
+        const T bb = A.rhs_from_V ? cable_rhs(A, si, gi, vi) : vi;
         const int q = sidx(lj - 1 - t, jj);
         sd[q] = dd;
         su[q] = ui;
