@@ -59,6 +59,22 @@ def parse():
     return ap.parse_args()
 
 
+def reduce_max(v: float, world: int, device: str) -> float:
+    """Largest v over the ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: int, steps: int, world: int, ms_total_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * steps * world / (ms_total_max * 1e-3)
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -195,11 +211,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, world, "cuda")
 
     plan = H.Plan(pop["ncomp"], pop["parent"])
     f32 = {k: torch.as_tensor(pop[k].astype(np.float32)).cuda() for k in ("d", "u", "b")}
@@ -245,7 +257,7 @@ def main():
     barrier()
     ms_total = max_over_ranks(e0.elapsed_time(e1))
     ms_step = ms_total / args.steps
-    value = n * args.steps * world / (ms_total * 1e-3)
+    value = job_value(n, args.steps, world, ms_total)
     status = plan.status()
 
     # parity on sampled cells against the oracle

@@ -1,0 +1,44 @@
+"""The multi-rank bookkeeping of bench.py (replicas, weak scaling) on CPU:
+two gloo ranks, each with its own time; the job's time is the slowest
+rank's and the value counts every rank's units."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = [120.0, 150.0][rank]
+        m = bench.reduce_max(ms, world, "cpu")
+        out[rank] = (m, bench.job_value(1000, 10, world, m))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(120)
+def test_two_gloo_ranks_take_the_slowest_time():
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_rank, args=(world, _free_port(), out), nprocs=world, start_method="spawn", join=True)
+    assert out[0] == out[1] == (150.0, 1000 * 10 * 2 / 0.150)
+
+
+def test_single_rank_needs_no_process_group():
+    assert not dist.is_initialized()
+    assert bench.reduce_max(3.5, 1, "cpu") == 3.5
+    assert bench.job_value(10, 4, 1, 2.0) == pytest.approx(20000.0)
