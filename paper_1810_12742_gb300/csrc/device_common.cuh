@@ -122,13 +122,16 @@ static __device__ __noinline__ double ff_to_double_slow(float hi, float lo) { re
 __device__ __forceinline__ double ff_to_double(float hi, float lo) {
   const uint32_t hb = __float_as_uint(hi);
   const uint32_t ex = (hb >> 23) & 0xFFu;
-  const float q = __fmul_rn(lo, __uint_as_float((306u - min(max(ex, 64u), 253u)) << 23));  // lo / ulp_double(hi)
-  int32_t k = __float2int_rn(q);
-  if (hb & 0x80000000u) k = -k;  // bits hold the magnitude
-  const bool slow = ex < 64u || ex > 253u || !(fabsf(q) < 1073741824.0f) || (k < 0 && (hb & 0x7FFFFFu) == 0u);
+  // lo / ulp_double(hi), signed against hi's magnitude: lo * (+-2^(179 - e)) with hi's sign
+  const float q = __fmul_rn(lo, __uint_as_float(((306u - ex) << 23) | (hb & 0x80000000u)));
+  const int32_t k = __float2int_rn(q);
+  // out of line: hi tiny or huge (biased exponent outside [64, 253]), lo not
+  // below hi's last place (or NaN), or a sum that drops below hi's binade
+  const bool slow = (ex - 64u) > 189u || !(fabsf(q) < 1073741824.0f) || (k < 0 && (hb & 0x7FFFFFu) == 0u);
   if (slow) return ff_to_double_slow(hi, lo);
-  const uint64_t db = ((uint64_t)(hb & 0x80000000u) << 32) | ((uint64_t)(ex + 896u) << 52) |
-                      ((uint64_t)(hb & 0x7FFFFFu) << 29);
+  // hi widened: exponent re-biased by 1023 - 127, mantissa moved up by 29 bits
+  const uint32_t whi = (((hb & 0x7FFFFFFFu) >> 3) + (896u << 20)) | (hb & 0x80000000u);
+  const uint64_t db = ((uint64_t)whi << 32) | (uint64_t)(hb << 29);
   return __longlong_as_double((long long)(db + (uint64_t)(int64_t)k));
 }
 
