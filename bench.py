@@ -370,6 +370,7 @@ def main():
     achieved = BYTES_F32_IN * n / (ms_step * 1e-3) / 1e9
     kernel = "k_units<CompMode>"
     tr = traffic_record(kernel)
+    tr_pk = traffic_record("k_units<CompModeT<solver layout>>")
     line = {
         "metric": metric, "value": value, "unit": "compartments/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -384,6 +385,7 @@ def main():
                  "max_rel_err": err64, "roofline_frac": BYTES_F64 * n / (ms64 * 1e-3) / 1e9 / peak,
                  "speedup_of_compensated": ms64 / ms_step},
         "solver_layout": {"value": n / (ms_pk * 1e-3), "unit": "compartments/s", "ms_per_solve": ms_pk,
+                          "traffic": None if tr_pk is None else tr_pk * n,
                           "max_rel_err": err_pk, "n_packed": plan.n_packed,
                           "roofline_frac": BYTES_F32_IN * n / (ms_pk * 1e-3) / 1e9 / peak,
                           "pack_d_u_b_ms": ms_pack, "unpack_x_ms": ms_unpack,
