@@ -180,8 +180,9 @@ struct CompModeT {
     double* x;
   };
   static constexpr int kStageBytes = 3 * kSlots * 4;
+  static constexpr int kStages = 2;
   static constexpr int kCacheBytes = 2 * 32 * 16 + 2 * 32 * 8 + kTabBytes;
-  static constexpr int kWarpBytes = 2 * kStageBytes + kCacheBytes;
+  static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);  // CTAs per SM that shared memory allows
 
   static constexpr bool kWantDs = true;
@@ -348,8 +349,11 @@ struct FactorMode {
     bool rhs_from_V;
   };
   static constexpr int kStageBytes = 3 * kSlots * (int)sizeof(T);
+  // FP64 chunks are large and the FP64 pipe is slow: one staging buffer, so
+  // that twice as many warps share an SM
+  static constexpr int kStages = sizeof(T) == 8 ? 1 : 2;
   static constexpr int kCacheBytes = 2 * 32 * 2 * (int)sizeof(T) + 2 * 32 * (int)sizeof(T) + kTabBytes;
-  static constexpr int kWarpBytes = 2 * kStageBytes + kCacheBytes;
+  static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);  // CTAs per SM that shared memory allows
 
   static constexpr bool kWantDs = false;
@@ -543,8 +547,8 @@ __device__ void run_task(const DevPlan& P, const typename M::Args& A, int t, int
   const int nl = P.task_nlvl[t];
   const int32_t* lp = P.tlvl_ptr + P.task_lvl_off[t];
   const int vb = code == 2 ? 1 : 0, ve = code == 1 ? 1 : 2;
-  unsigned char* cache = wbase + 2 * M::kStageBytes;
-  auto buf = [wbase](int which) { return wbase + which * M::kStageBytes; };
+  unsigned char* cache = wbase + M::kStages * M::kStageBytes;
+  auto buf = [wbase](int which) { return wbase + (M::kStages == 2 ? which : 0) * M::kStageBytes; };
   auto meta = [&](const Pos& p) {
     return load_meta<M::kPacked>(P, p.c0 + lane, p.visit < ve && lane < p.n, M::kWantDs && p.visit == 1);
   };
@@ -561,7 +565,9 @@ __device__ void run_task(const DevPlan& P, const typename M::Args& A, int t, int
     // nothing of the substitution is read before the elimination has finished:
     // its first chunks reuse positions the elimination is still writing
     const bool crossing = nxt.visit != cur.visit;
-    if (nxt.visit < ve && !crossing) M::stage(P, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1));
+    // two staging buffers: the next chunk is copied in while this one is
+    // computed; one buffer: after this one is done (more warps per SM instead)
+    if (M::kStages == 2 && nxt.visit < ve && !crossing) M::stage(P, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1));
     const Pos nn = nxt.visit < ve ? pos_next(nxt, lp, nl, ve) : nxt;
     Meta m_nn = meta(nn);
     M::compute(P, A, cur.visit, cur.c0, cur.n, lane, m_cur, buf(which), pv, cache, cur.l & 1);
@@ -571,8 +577,8 @@ __device__ void run_task(const DevPlan& P, const typename M::Args& A, int t, int
     if (crossing && nxt.visit < ve) {
       m_nxt = meta(nxt);
       m_nn = meta(nn);
-      M::stage(P, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1));
     }
+    if (nxt.visit < ve && (crossing || M::kStages == 1)) M::stage(P, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1));
     // predecessor of the next chunk: the last chunk of the level before its level, same sweep
     if (crossing) {
       pv = Prev{0, 0, 0};
