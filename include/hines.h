@@ -67,9 +67,9 @@ typedef struct {
                               inspected with hines_plan_info / hines_plan_export but not solved */
   int32_t split_branches;  /* 1: split branches longer than their level's mean (Section 6) */
   int32_t cta_threads;     /* threads per CTA of the level-synchronous kernels (0: 256) */
-  int32_t sort_by_length;  /* 1: within a level of a warp task, order branches by length (descending;
-                              Section 4, Fig. 4.1); 0: by memory order, so that a chunk of 32
-                              branches of a breadth-first numbered cell is one contiguous range */
+  int32_t sort_by_length;  /* 1: among ready branches equally far from their unit root, take the
+                              longer first (Section 4, Fig. 4.1); 0: by cell and branch index,
+                              so that a chunk of a breadth-first numbered cell reads contiguous runs */
   int32_t pack_compartments; /* warp tasks are filled with units up to this many compartments
                                 (0: 24576); -1: Section 4's rule instead (a unit joins a task
                                 while every level of the task holds at most 32 branches) */
@@ -102,12 +102,14 @@ typedef struct {
  * p[i] != i-1, or p[i] has two or more children), optionally splits branches
  * longer than their level's mean (Section 6), cuts every branch longer than
  * 16 compartments into near-equal chained pieces, assigns levels (number of
- * ancestor branches), orders the branches of every level by length
- * (descending, ties by branch index; Section 4, Fig. 4.1), packs cells into
- * warp tasks (Section 4's greedy rule with the 32 lanes of a warp: cells are
- * added, largest first, while every level of the task holds at most 32
- * branches), and uploads the metadata and a workspace to the current device.
- * On success *out receives the plan; on failure *out is NULL.
+ * ancestor branches), cuts cells of more than 4096 compartments into a top
+ * part and subtrees, packs these units into warp tasks (by size, or by
+ * Section 4's greedy rule with the 32 lanes of a warp), cuts every task into
+ * chunks of at most 32 branches by Hu's list schedule (a branch joins a chunk
+ * once its children in the task are in earlier chunks, deepest first), lays
+ * out the solver layout (Section 5), and uploads the metadata and a workspace
+ * to the current device.  On success *out receives the plan; on failure *out
+ * is NULL.
  */
 hines_status hines_plan_create(hines_plan_t *out, int32_t n_cells, const int32_t *ncomp, const int32_t *parent,
                                const hines_plan_opts *opts);
@@ -140,14 +142,17 @@ hines_status hines_plan_export(hines_plan_t plan, int64_t *first, int64_t *len, 
  * at most 4096 compartments is one unit; a larger cell is cut into its top
  * part (the branches whose subtree holds more than 4096 compartments) and one
  * unit per subtree hanging below the top part.  Units of one kind are packed
- * into tasks, largest first, while every level (counted from each unit's root
- * branch) holds at most 32 branches (Section 4's rule with 32 lanes).
+ * into tasks, largest first (subtrees per cell), up to pack_compartments
+ * compartments, or with the lane rule while every level (counted from each
+ * unit's root branch) holds at most 32 branches (Section 4's rule).
  *   branch_task[nb]  task of each branch
  *   branch_kind[nb]  kind of the branch's unit: 0 whole cell, 1 subtree, 2 top part
  *   task_order[nb]   branches in processing order: tasks whole-cell, then
- *        subtree, then top kind, each largest first; within a task by level
- *        from the unit roots, then cell, then branch index (with
- *        sort_by_length: by length descending first)
+ *        subtree, then top kind; within a task the chunks of Hu's list schedule
+ *        (at most 32 branches each; a branch follows all its children in the
+ *        task; ready branches farthest from the unit root first, ties by
+ *        length descending with sort_by_length, then cell, then branch index),
+ *        listed root-side chunk first
  */
 hines_status hines_plan_export_tasks(hines_plan_t plan, int64_t *branch_task, int64_t *branch_kind,
                                      int64_t *task_order);
