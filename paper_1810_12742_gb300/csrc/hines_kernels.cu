@@ -1,16 +1,17 @@
-// CUDA kernels of the batched Hines solver, sm_103a.
+// CUDA kernels of the batched Hines solver, sm_103a: the FP32 + FP64
+// refinement solve and the adjoint's elementwise gathers.
 //
-// Level-synchronous branch-parallel solve (Section 3): one CTA owns one cell;
-// the branches of a level are processed in parallel, one thread per branch,
-// deepest level first for the elimination and root level first for the
-// substitution, with a CTA barrier between levels.  Inside a branch the
-// parent of compartment i is i - 1 (Section 5), so a thread runs a Thomas
-// chain (Listing 1); at the branch's proximal end the elimination produces
-// one contribution to the parent compartment (Listing 2's parent lookup),
-// which the parent branch's thread folds in before its own chain starts.
-// Child contributions go through per-branch slots, so siblings never write
-// the same word and the fold order is fixed (children by first compartment,
-// descending).
+// k_solve_refine is level-synchronous and branch-parallel (Section 3): one CTA
+// owns one cell; the branches of a level are processed in parallel, one
+// thread per branch, deepest level first for the elimination and root level
+// first for the substitution, with a CTA barrier between levels.  Inside a
+// branch the parent of compartment i is i - 1 (Section 5), so a thread runs a
+// Thomas chain (Listing 1); at the branch's proximal end the elimination
+// produces one contribution to the parent compartment (Listing 2's parent
+// lookup), which the parent branch's thread folds in before its own chain
+// starts.  Child contributions go through per-branch slots, so siblings never
+// write the same word and the fold order is fixed (children by first
+// compartment, descending).
 #include <cfloat>
 
 #include "kernels.h"
@@ -18,119 +19,6 @@
 
 namespace hines {
 namespace {
-
-// ----------------------------------------------------------------------------
-// System sources: how the elimination reads d_i and b_i.
-// ----------------------------------------------------------------------------
-// Plain solve: d and b are given.
-template <typename T>
-struct PlainSys {
-  const T* d;
-  const T* b;  // right-hand side (the in/out array)
-  __device__ __forceinline__ T diag(int64_t i, bool, bool) const { return d[i]; }
-  __device__ __forceinline__ T rhs(int64_t i) const { return b[i]; }
-  static constexpr bool kEdgeDiag = false;
-};
-
-// Passive cable (Section 1 system): d_i = s_i (1 + theta dt g_i) + sum of a
-// over the edges at i, with a = -u; b_i = s_i V_i + s_i dt g_i (E - (1-theta) V_i).
-// The sum over child-branch edges is folded in with the child contributions.
-struct CableSys {
-  const double* s;
-  const double* g;
-  const double* u;
-  const double* V;  // the in/out array
-  double dt, E, theta;
-  bool rhs_from_V;  // false: the in/out array already holds the right-hand side
-  __device__ __forceinline__ double diag(int64_t i, bool parent_edge, bool chain_child) const {
-    double v = s[i] * (1.0 + theta * dt * g[i]);
-    if (parent_edge) v -= u[i];
-    if (chain_child) v -= u[i + 1];
-    return v;
-  }
-  __device__ __forceinline__ double rhs(int64_t i) const {
-    if (!rhs_from_V) return V[i];
-    const double vi = V[i];
-    return s[i] * vi + s[i] * dt * g[i] * (E - (1.0 - theta) * vi);
-  }
-  static constexpr bool kEdgeDiag = true;
-};
-
-// ----------------------------------------------------------------------------
-// Level-synchronous solve, CTA per cell.  fac receives the eliminated
-// diagonal d'_i, the in/out array x first the eliminated right-hand side b'_i
-// and then the solution.
-// ----------------------------------------------------------------------------
-template <typename T, typename Sys>
-__global__ void __launch_bounds__(1024) k_solve_cell(DevPlan P, Sys sys, const T* __restrict__ u, T* x) {
-  const int32_t cell = P.task_cell[blockIdx.x];
-  const int32_t nl = P.cell_nlvl[cell];
-  if (nl == 0) return;
-  const int32_t* lp = P.lvl_ptr + P.cell_lvl_off[cell];
-  T* fac = static_cast<T*>(P.fac);
-  T* cd = static_cast<T*>(P.cd);
-  T* cb = static_cast<T*>(P.cb);
-
-  // backward substitution, leaves to root (Listing 2, first loop)
-  for (int l = nl - 1; l >= 0; --l) {
-    for (int k = lp[l] + (int)threadIdx.x; k < lp[l + 1]; k += blockDim.x) {
-      const int32_t br = P.order[k];
-      const int64_t f0 = P.br_first[br];
-      const int64_t last = f0 + P.br_len[br] - 1;
-      const bool has_parent = P.br_parent[br] >= 0;
-      int64_t i = last;
-      T cur_d = sys.diag(i, i > f0 || has_parent, false);
-      T cur_b = sys.rhs(i);
-      for (int32_t c = P.child_ptr[br]; c < P.child_ptr[br + 1]; ++c) {
-        const int32_t ch = P.child[c];
-        cur_d -= cd[ch];
-        cur_b -= cb[ch];
-      }
-      for (; i > f0; --i) {
-        fac[i] = cur_d;
-        x[i] = cur_b;
-        const T ui = u[i];
-        const T f = ui / cur_d;
-        cur_d = sys.diag(i - 1, i - 1 > f0 || has_parent, true) - f * ui;
-        cur_b = sys.rhs(i - 1) - f * cur_b;
-      }
-      fac[f0] = cur_d;
-      if (has_parent) {
-        x[f0] = cur_b;
-        const T ui = u[f0];
-        const T f = ui / cur_d;
-        cd[br] = Sys::kEdgeDiag ? f * ui + ui : f * ui;
-        cb[br] = f * cur_b;
-      } else {
-        x[f0] = cur_b / cur_d;  // solve root
-      }
-    }
-    __syncthreads();
-  }
-  // forward substitution, root to leaves (Listing 2, second loop)
-  for (int l = 0; l < nl; ++l) {
-    for (int k = lp[l] + (int)threadIdx.x; k < lp[l + 1]; k += blockDim.x) {
-      const int32_t br = P.order[k];
-      const int64_t f0 = P.br_first[br];
-      const int64_t end = f0 + P.br_len[br];
-      const int32_t pb = P.br_parent[br];
-      int64_t i = f0;
-      T xp;
-      if (pb < 0) {
-        xp = x[f0];
-        ++i;
-      } else {
-        xp = x[P.br_first[pb] + P.br_len[pb] - 1];
-      }
-      for (; i < end; ++i) {
-        const T xi = (x[i] - u[i] * xp) / fac[i];
-        x[i] = xi;
-        xp = xi;
-      }
-    }
-    __syncthreads();
-  }
-}
 
 // ----------------------------------------------------------------------------
 // Mixed precision: FP32 elimination, FP64 residual and correction.
@@ -370,40 +258,10 @@ int grid_for_branches(const DevPlan& P) {
 
 }  // namespace
 
-cudaError_t launch_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s) {
-  if (P.n_tasks == 0) return cudaSuccess;
-  PlainSys<double> sys{d, b};
-  k_solve_cell<double, PlainSys<double>><<<P.n_tasks, P.cta_threads, 0, s>>>(P, sys, u, b);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s) {
-  if (P.n_tasks == 0) return cudaSuccess;
-  PlainSys<float> sys{d, b};
-  k_solve_cell<float, PlainSys<float>><<<P.n_tasks, P.cta_threads, 0, s>>>(P, sys, u, b);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_solve_refine(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
                                 int steps, double* relres, cudaStream_t s) {
   if (P.n_tasks == 0) return cudaSuccess;
   k_solve_refine<<<P.n_tasks, P.cta_threads, 0, s>>>(P, d, u, b, x, steps, relres);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cable_step(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
-                              double dt, double E, int theta, cudaStream_t s) {
-  if (P.n_tasks == 0) return cudaSuccess;
-  CableSys sys{sv, g, u, V, dt, E, (double)theta, true};
-  k_solve_cell<double, CableSys><<<P.n_tasks, P.cta_threads, 0, s>>>(P, sys, u, V);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cable_solve(const DevPlan& P, const double* sv, const double* g, const double* u, double* y,
-                               double dt, int theta, cudaStream_t s) {
-  if (P.n_tasks == 0) return cudaSuccess;
-  CableSys sys{sv, g, u, y, dt, 0.0, (double)theta, false};
-  k_solve_cell<double, CableSys><<<P.n_tasks, P.cta_threads, 0, s>>>(P, sys, u, y);
   return cudaGetLastError();
 }
 

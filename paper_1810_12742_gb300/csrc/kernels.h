@@ -21,11 +21,11 @@ struct __align__(16) BrMetaT {
 // the plan's workspace.
 struct DevPlan {
   int32_t n_cells = 0;
-  int32_t n_tasks = 0;          // cells, for the CTA-per-cell kernels
+  int32_t n_tasks = 0;          // cells, for the refinement kernel (one CTA per cell)
   int32_t cta_threads = 256;
   int64_t n_unknowns = 0;
   int64_t n_branches = 0;
-  // CTA-per-cell level-synchronous kernels
+  // refinement kernel (level-synchronous, one CTA per cell) and adjoint gathers
   const int64_t* cell_off = nullptr;      // [n_cells + 1]
   const int32_t* task_cell = nullptr;     // [n_cells] cells, most compartments first
   const int32_t* cell_nlvl = nullptr;     // [n_cells]
@@ -60,7 +60,7 @@ struct DevPlan {
   void* fac = nullptr;    // 8 bytes per natural or solver-layout slot: factor (FP64 / FP32 solves), FP32 working
                           // arrays (refine)
   void* cd = nullptr;     // n_branches * 16 bytes: child-to-parent contribution (or root solution) per position
-  void* cb = nullptr;     // n_branches * 8 bytes: FP32/FP64 per-branch contribution (CTA-per-cell kernels)
+  void* cb = nullptr;     // n_branches * 8 bytes: FP32/FP64 per-branch contribution (refinement kernel)
   void* dstate = nullptr; // n_branches * 16 bytes: folded distal state per position (compensated)
   void* xlast = nullptr;  // n_branches * 8 bytes: solution at the distal compartment per position
   void* red = nullptr;    // n_cells * 8 bytes: per-cell reductions
@@ -87,15 +87,9 @@ cudaError_t launch_pk_cable(const DevPlan& P, const double* sv, const double* g,
 cudaError_t launch_pack(const DevPlan& P, int elem_bytes, const void* natural, void* packed, cudaStream_t s);
 cudaError_t launch_unpack(const DevPlan& P, int elem_bytes, const void* packed, void* natural, cudaStream_t s);
 
-// CTA-per-cell kernels (hines_kernels.cu).
-cudaError_t launch_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s);
-cudaError_t launch_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s);
+// Refinement solve and adjoint gathers (hines_kernels.cu).
 cudaError_t launch_solve_refine(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
                                 int steps, double* relres, cudaStream_t s);
-cudaError_t launch_cable_step(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
-                              double dt, double E, int theta, cudaStream_t s);
-cudaError_t launch_cable_solve(const DevPlan& P, const double* sv, const double* g, const double* u, double* y,
-                               double dt, int theta, cudaStream_t s);
 cudaError_t launch_grad_du(const DevPlan& P, const double* lam, const double* x, double* gd, double* gu,
                            cudaStream_t s);
 cudaError_t launch_cable_adjoint_step(const DevPlan& P, const double* lam, const double* Vk, const double* Vkm1,
