@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--refine-reps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (64-cell, 16384-cell, margin sweep, adjoint)")
     ap.add_argument("--cable-steps", type=int, default=100,
                     help="passive-cable steps per captured graph for the time-stepping figure (0: skip)")
     ap.add_argument("--only", choices=["headline", "solver_layout"],
@@ -164,6 +166,133 @@ def cpu_baseline(pop, widen, budget_s=12.0):
     return {"value": n * reps / el, "unit": "compartments/s", "cores": nthreads, "kind": "oracle",
             "sample": f"{reps} x the full batch ({n} compartments), serial FP64 Hines solve per cell, "
                       f"OpenMP over cells"}
+
+
+def _timed_ms(torch, stream, fn, reps, warm=3):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        fn()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    return a0.elapsed_time(a1) / reps
+
+
+def _cell_err(x, ref, off, cells):
+    e = 0.0
+    for j, c in enumerate(cells):
+        sl = slice(off[c], off[c + 1])
+        if off[c + 1] > off[c]:
+            e = max(e, float(np.abs(x[sl] - ref[j]).max() / np.abs(ref[j]).max()))
+    return e
+
+
+def other_configs(torch, H, oracle, stream, max_over_ranks):
+    """The other workloads, each on the GPU against the oracle: the 64-cell
+    FP64 solve (latency), the 16384-cell FP64 batch, the leak-margin sweep of
+    the FP32-input solves on a subset of the uneven population, and the
+    200-step adjoint."""
+    from paper_1810_12742_gb300 import inputs as I
+    from paper_1810_12742_gb300 import rollout as R
+    out = {}
+    peak = load_peaks()[0]
+    nth = os.cpu_count() or 1
+
+    def oracle_cells(pop, cells, widen=False):
+        off = pop["offsets"]
+        refs = []
+        for c in cells:
+            sl = slice(off[c], off[c + 1])
+            arrs = [pop[k][sl].astype(np.float32).astype(np.float64) if widen else pop[k][sl]
+                    for k in ("d", "u", "b")]
+            refs.append(oracle.solve_batch(pop["ncomp"][c:c + 1], pop["parent"][sl], *arrs))
+        return refs
+
+    # 64 binary cells x 248 compartments, FP64: launch/latency bound
+    pop = I.population("fp64_small")
+    plan = H.Plan(pop["ncomp"], pop["parent"])
+    d, u, b = (torch.as_tensor(pop[k]).cuda() for k in ("d", "u", "b"))
+    x = b.clone()
+    us = max_over_ranks(_timed_ms(torch, stream, lambda: H.solve(plan, d, u, x), 200) * 1e3)
+    x = b.clone()
+    H.solve(plan, d, u, x)
+    cells = np.arange(pop["ncomp"].size)
+    out["fp64_small"] = {"us_per_solve": us, "compartments": int(pop["offsets"][-1]),
+                         "max_rel_err": _cell_err(x.cpu().numpy(), oracle_cells(pop, cells), pop["offsets"], cells)}
+    del plan
+
+    # 16384 cells, about 59M compartments, FP64
+    pop = I.population("fp64_uniform")
+    n1 = int(pop["offsets"][-1])
+    plan = H.Plan(pop["ncomp"], pop["parent"])
+    d, u, b = (torch.as_tensor(pop[k]).cuda() for k in ("d", "u", "b"))
+    x = b.clone()
+    ms = max_over_ranks(_timed_ms(torch, stream, lambda: H.solve(plan, d, u, x), 10))
+    x = b.clone()
+    H.solve(plan, d, u, x)
+    cells = np.sort(np.random.default_rng(2).choice(pop["ncomp"].size, 32, replace=False))
+    out["fp64_uniform"] = {"ms_per_solve": ms, "compartments": n1, "compartments_per_s": n1 / (ms * 1e-3),
+                           "hbm_frac_32B": 32 * n1 / (ms * 1e-3) / 1e9 / peak,
+                           "max_rel_err": _cell_err(x.cpu().numpy(), oracle_cells(pop, cells), pop["offsets"], cells)}
+    del plan, d, u, b, x, pop
+
+    # leak-margin sweep, FP32 inputs: 256 cells of the uneven population (both classes)
+    w = I.WORKLOADS["uneven_mixed"]
+    cls = I.cell_classes(w)
+    sub = np.concatenate([np.nonzero(cls == 0)[0][:180], np.nonzero(cls == 1)[0][:76]])
+    sweep = {}
+    for m in I.MARGINS:
+        pop = I.population(w, cells=sub, margin=m)
+        plan = H.Plan(pop["ncomp"], pop["parent"])
+        f32 = {k: torch.as_tensor(pop[k].astype(np.float32)).cuda() for k in ("d", "u", "b")}
+        cells = np.arange(sub.size)
+        refs = oracle_cells(pop, cells, widen=True)
+        wd = {k: pop[k].astype(np.float32).astype(np.float64) for k in ("d", "u")}
+        cond = oracle.skeel_batch(pop["ncomp"], pop["parent"], wd["d"], wd["u"], np.concatenate(refs), nth)
+        xc = H.solve_compensated(plan, f32["d"], f32["u"], f32["b"]).cpu().numpy()
+        xf = f32["b"].clone()
+        H.solve(plan, f32["d"], f32["u"], xf)
+        r = {"skeel_cond_max": float(cond.max()),
+             "compensated": _cell_err(xc, refs, pop["offsets"], cells),
+             "fp32": _cell_err(xf.double().cpu().numpy(), refs, pop["offsets"], cells)}
+        for st in (1, 2):
+            xr = H.solve_refine(plan, f32["d"], f32["u"], f32["b"], steps=st).cpu().numpy()
+            r[f"fp32_refine_{st}"] = _cell_err(xr, refs, pop["offsets"], cells)
+        sweep[f"{m:g}"] = r
+        del plan, f32
+    out["margin_sweep"] = {"cells": int(sub.size), "max_rel_err": sweep}
+
+    # adjoint: 256 cells, 200 implicit-Euler steps, checkpoints every 20
+    w = I.WORKLOADS["adjoint"]
+    pop = I.population(w, keys=("s", "a", "u", "g", "V0", "target"))
+    plan = H.Plan(pop["ncomp"], pop["parent"])
+    tt = {k: torch.as_tensor(pop[k]).cuda() for k in ("s", "a", "g", "V0", "target")}
+    ga = tt["g"].clone().requires_grad_(True)
+    aa = tt["a"].clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = R.CableRollout.apply(ga, aa, plan, tt["s"], tt["V0"], tt["target"], w.steps, w.dt, w.E, 1,
+                             w.checkpoint_every)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    L.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    loss, rg, ra = oracle.adjoint_batch(pop["ncomp"], pop["parent"], pop["s"], pop["g"], pop["a"], pop["V0"],
+                                        pop["target"], w.steps, w.dt, w.E, 1, nthreads=nth)
+    gg, gaa = ga.grad.cpu().numpy(), aa.grad.cpu().numpy()
+    roots = pop["offsets"][:-1]
+    mask = np.ones(gaa.size, bool)
+    mask[roots] = False
+    out["adjoint"] = {"steps": w.steps, "compartments": int(pop["offsets"][-1]),
+                      "forward_ms": (t1 - t0) * 1e3, "backward_ms": (t2 - t1) * 1e3,
+                      "loss_rel_err": abs(L.item() - float(loss.sum())) / abs(float(loss.sum())),
+                      "grad_g_rel_err": float(np.abs(gg - rg).max() / np.abs(rg).max()),
+                      "grad_a_rel_err": float(np.abs(gaa[mask] - ra[mask]).max() / np.abs(ra[mask]).max())}
+    return out
 
 
 def main():
@@ -375,6 +504,8 @@ def main():
             del st, V
         del cs, cp
 
+    configs = None if (args.no_configs or args.cells) else other_configs(torch, H, oracle, stream, max_over_ranks)
+
     # end to end through the public API with pinned host buffers
     host = {k: torch.as_tensor(pop[k].astype(np.float32)).pin_memory() for k in ("d", "u", "b")}
     xh = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -406,6 +537,7 @@ def main():
                           "pack_d_u_b_ms": ms_pack, "unpack_x_ms": ms_unpack,
                           "path": "hines_solve_compensated_packed on d, u, b, x kept in the solver layout"},
         "cable_steps": cable,
+        "configs": configs,
         "fp32_refine": {"value": n / (ms_ref * 1e-3), "unit": "compartments/s", "ms_per_solve": ms_ref,
                         "refine_steps": args.refine_steps, "max_rel_err": err_ref,
                         "roofline_frac": BYTES_F32_IN * n / (ms_ref * 1e-3) / 1e9 / peak},

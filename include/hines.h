@@ -71,7 +71,8 @@ typedef struct {
                               longer first (Section 4, Fig. 4.1); 0: by cell and branch index,
                               so that a chunk of a breadth-first numbered cell reads contiguous runs */
   int32_t pack_compartments; /* warp tasks are filled with units up to this many compartments
-                                (0: 24576); -1: Section 4's rule instead (a unit joins a task
+                                (0: 24576, or total / 2048 for smaller batches, so that they still
+                                give one task per warp); -1: Section 4's rule instead (a unit joins a task
                                 while every level of the task holds at most 32 branches) */
   int32_t reserved[3];     /* must be zero */
 } hines_plan_opts;

@@ -309,7 +309,12 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
   // while every relative level holds at most kLanes branches (Section 4's
   // rule with the 32 lanes of a warp)
   const bool lane_rule = pack_compartments < 0;
-  const int64_t pack_max = pack_compartments > 0 ? pack_compartments : kTaskCompartments;
+  // default fill: kTaskCompartments, but small enough that a small batch
+  // still gives kMinTasks tasks (one per warp of a full GPU) where its units allow
+  const int64_t pack_max =
+      pack_compartments > 0
+          ? pack_compartments
+          : std::min<int64_t>(kTaskCompartments, std::max<int64_t>(1, (P.n_unknowns + kMinTasks - 1) / kMinTasks));
   P.n_tasks = 0;
   P.task_kind.clear();
   P.task_nlvl.clear();

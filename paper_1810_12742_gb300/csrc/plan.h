@@ -72,6 +72,7 @@ constexpr int kWarpsPerCta = 4;  // warps per CTA of the task kernels (each warp
 constexpr int64_t kUnitMax = 4096;  // largest unit (compartments); larger cells are cut
 constexpr int64_t kPackAlign = 4;   // solver-layout blocks start on multiples of 4 compartments
 constexpr int64_t kTaskCompartments = 24576;  // default fill of a warp task
+constexpr int64_t kMinTasks = 2048;           // smaller tasks for batches below kMinTasks * kTaskCompartments
 
 // Return codes follow hines_status.
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,

@@ -188,7 +188,7 @@ def py_hu(ids, rl, sort_by_length):
 G = {}
 
 
-def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=24576):
+def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0):
     off = np.concatenate(([0], np.cumsum(ncomp))).astype(np.int64)
     cells = [py_branches(parent[off[c]:off[c + 1]]) for c in range(len(ncomp))]
     if split:
@@ -214,6 +214,8 @@ def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=24576):
     base_of = np.concatenate(([0], np.cumsum([len(bs) for bs in cells]))).astype(np.int64)
     cells_flat = [list(range(base_of[c], base_of[c + 1])) for c in range(len(cells))]
     units = py_units(list(ncomp), cells_flat)
+    if pack == 0:  # default: 24576, smaller so that a small batch gives 2048 tasks where units allow
+        pack = min(24576, max(1, -(-int(np.sum(ncomp)) // 2048)))
     tasks = py_tasks(list(ncomp), units, sort_by_length, pack)
     nb = len(first)
     branch_task = np.full(nb, -1, np.int64)
@@ -236,7 +238,7 @@ def _compare(ncomp, parent, split, sort_by_length=False, pack=0):
                   pack_compartments=pack)
     got = plan.export()
     got.update(plan.export_tasks())
-    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split, sort_by_length, pack if pack else 24576)
+    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split, sort_by_length, pack)
     assert plan.n_tasks == ref.pop("n_tasks")
     for k in ref:
         assert np.array_equal(got[k], ref[k]), k
