@@ -357,7 +357,9 @@ def main():
     def max_over_ranks(v):
         return reduce_max(v, world, "cuda")
 
+    t_plan = time.perf_counter()
     plan = H.Plan(pop["ncomp"], pop["parent"])
+    config["plan_create_s"] = time.perf_counter() - t_plan  # host planner + upload, once per morphology
     f32 = {k: torch.as_tensor(pop[k].astype(np.float32)).cuda() for k in ("d", "u", "b")}
     x = torch.empty(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()

@@ -54,4 +54,14 @@ def test_argument_errors_without_gpu():
     plan = H.Plan(nc, pa, host_only=True)
     # a host-only plan refuses device work before touching CUDA
     assert L.hines_solve(plan.handle, H.HINES_F64, None, None, None, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_solve_compensated(plan.handle, None, None, None, None, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_solve_packed(plan.handle, H.HINES_F32, None, None, None, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_solve_compensated_packed(plan.handle, None, None, None, None, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_pack(plan.handle, 4, None, None, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_unpack(plan.handle, 8, None, None, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_cable_step_packed(plan.handle, None, None, None, None, 0.025, -65.0, 1, None) == \
+        H.HINES_ERR_INVALID_ARG
+    # but its solver layout can be inspected: 2 compartments in one chunk, padded to 4 slots
+    assert plan.n_packed == 4
+    assert plan.export_packed().tolist() == [1, 0, -1, -1]
     assert L.hines_plan_destroy(None) == H.HINES_OK
