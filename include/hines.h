@@ -66,7 +66,8 @@ typedef struct {
   int32_t host_only;       /* 1: build the host-side plan only (no CUDA calls); it can be
                               inspected with hines_plan_info / hines_plan_export but not solved */
   int32_t split_branches;  /* 1: split branches longer than their level's mean (Section 6) */
-  int32_t cta_threads;     /* threads per CTA of the level-synchronous refinement kernel (0: 256) */
+  int32_t cta_threads;     /* 0, or a multiple of 32 in 32..1024 (validated; no kernel of this
+                              version takes a CTA size from it) */
   int32_t sort_by_length;  /* 1: among ready branches equally far from their unit root, take the
                               longer first (Section 4, Fig. 4.1); 0: by cell and branch index,
                               so that a chunk of a breadth-first numbered cell reads contiguous runs */

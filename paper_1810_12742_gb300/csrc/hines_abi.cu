@@ -28,7 +28,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Copy the host plan's arrays into one device allocation and point the
 // device view at them; allocate the workspace.
-hines_status upload(hines_plan_t p, int cta_threads) {
+hines_status upload(hines_plan_t p) {
   const hines::HostPlan& H = p->host;
   struct Item {
     const void* src;
@@ -77,14 +77,11 @@ hines_status upload(hines_plan_t p, int cta_threads) {
       {H.counter_init.data(), H.counter_init.size() * 4, (const void**)&D.counter_init},
       {H.task_sub.data(), H.task_sub.size() * 4, (const void**)&D.task_sub},
       {H.cell_off.data(), H.cell_off.size() * 8, (const void**)&D.cell_off},
-      {H.task_cell.data(), H.task_cell.size() * 4, (const void**)&D.task_cell},
-      {H.cell_nlvl.data(), H.cell_nlvl.size() * 4, (const void**)&D.cell_nlvl},
-      {H.cell_lvl_off.data(), H.cell_lvl_off.size() * 8, (const void**)&D.cell_lvl_off},
-      {H.lvl_ptr.data(), H.lvl_ptr.size() * 4, (const void**)&D.lvl_ptr},
-      {H.order.data(), H.order.size() * 4, (const void**)&D.order},
       {H.br_first.data(), H.br_first.size() * 8, (const void**)&D.br_first},
       {H.br_len.data(), H.br_len.size() * 4, (const void**)&D.br_len},
       {H.br_parent.data(), H.br_parent.size() * 4, (const void**)&D.br_parent},
+      {H.br_cell.data(), H.br_cell.size() * 4, (const void**)&D.br_cell},
+      {H.cell_br_off.data(), H.cell_br_off.size() * 8, (const void**)&D.cell_br_off},
       {H.child_ptr.data(), H.child_ptr.size() * 4, (const void**)&D.child_ptr},
       {H.child.data(), H.child.size() * 4, (const void**)&D.child},
   };
@@ -109,7 +106,7 @@ hines_status upload(hines_plan_t p, int cta_threads) {
   const size_t n = (size_t)H.n_unknowns, nb = H.br_first.size(), nc = (size_t)H.n_cells;
   // the factor is indexed by natural or solver-layout position
   const size_t fac_b = align256(std::max(n, (size_t)H.n_packed) * 8 + 8), cd_b = align256(nb * 16 + 16),
-               cb_b = align256(nb * 8 + 8),
+               cb_b = align256(nb * 32 + 32),
                ds_b = align256(nb * 16 + 16), xl_b = align256(nb * 8 + 8), red_b = align256(nc * 8 + 8),
                cnt_b = align256((nc + 4) * 4);
   const size_t wtotal = fac_b + cd_b + cb_b + ds_b + xl_b + red_b + cnt_b;
@@ -138,8 +135,6 @@ hines_status upload(hines_plan_t p, int cta_threads) {
   D.n_packed = H.n_packed;
   for (int k = 0; k < 4; ++k) D.phase_off[k] = H.phase_off.empty() ? 0 : H.phase_off[(size_t)k];
   D.n_cells = H.n_cells;
-  D.n_tasks = H.n_cells;
-  D.cta_threads = cta_threads;
   D.n_unknowns = H.n_unknowns;
   D.n_branches = (int64_t)nb;
   if (hines::prepare_unit_kernels(D) != cudaSuccess) return HINES_ERR_CUDA;
@@ -194,7 +189,7 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
       delete p;
       return HINES_ERR_CUDA;
     }
-    hines_status st = upload(p, o.cta_threads);
+    hines_status st = upload(p);
     if (st != HINES_OK) {
       hines_plan_destroy(p);
       return st;
@@ -346,8 +341,8 @@ hines_status hines_solve_refine(hines_plan_t p, const float* d, const float* u, 
   if (st != HINES_OK) return st;
   if (!need(p, d) || !need(p, u) || !need(p, b) || !need(p, x_out)) return HINES_ERR_INVALID_ARG;
   if (refine_steps < 0 || refine_steps > 4) return HINES_ERR_INVALID_ARG;
-  return launched(hines::launch_solve_refine(p->dev, d, u, b, x_out, refine_steps, cell_relres,
-                                             reinterpret_cast<cudaStream_t>(stream)));
+  return launched(hines::launch_unit_refine(p->dev, d, u, b, x_out, refine_steps, cell_relres,
+                                            reinterpret_cast<cudaStream_t>(stream)));
 }
 
 hines_status hines_cable_step(hines_plan_t p, const double* s, const double* g, const double* u, double* V_inout,

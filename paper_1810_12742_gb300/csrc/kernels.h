@@ -21,20 +21,15 @@ struct __align__(16) BrMetaT {
 // the plan's workspace.
 struct DevPlan {
   int32_t n_cells = 0;
-  int32_t n_tasks = 0;          // cells, for the refinement kernel (one CTA per cell)
-  int32_t cta_threads = 256;
   int64_t n_unknowns = 0;
   int64_t n_branches = 0;
-  // refinement kernel (level-synchronous, one CTA per cell) and adjoint gathers
+  // branches in the natural layout (refinement residual, adjoint gathers)
   const int64_t* cell_off = nullptr;      // [n_cells + 1]
-  const int32_t* task_cell = nullptr;     // [n_cells] cells, most compartments first
-  const int32_t* cell_nlvl = nullptr;     // [n_cells]
-  const int64_t* cell_lvl_off = nullptr;  // [n_cells]
-  const int32_t* lvl_ptr = nullptr;       // per cell nlvl + 1
-  const int32_t* order = nullptr;         // [nb]
   const int64_t* br_first = nullptr;      // [nb]
   const int32_t* br_len = nullptr;        // [nb]
   const int32_t* br_parent = nullptr;     // [nb]
+  const int32_t* br_cell = nullptr;       // [nb]
+  const int64_t* cell_br_off = nullptr;   // [n_cells + 1] branches of each cell
   const int32_t* child_ptr = nullptr;     // [nb + 1]
   const int32_t* child = nullptr;         // [nb - roots]
   // warp tasks over units (whole cells, subtrees, top parts)
@@ -60,7 +55,7 @@ struct DevPlan {
   void* fac = nullptr;    // 8 bytes per natural or solver-layout slot: factor (FP64 / FP32 solves), FP32 working
                           // arrays (refine)
   void* cd = nullptr;     // n_branches * 16 bytes: child-to-parent contribution (or root solution) per position
-  void* cb = nullptr;     // n_branches * 8 bytes: FP32/FP64 per-branch contribution (refinement kernel)
+  void* cb = nullptr;     // n_branches * 32 bytes: per-branch reductions of the refinement
   void* dstate = nullptr; // n_branches * 16 bytes: folded distal state per position (compensated)
   void* xlast = nullptr;  // n_branches * 8 bytes: solution at the distal compartment per position
   void* red = nullptr;    // n_cells * 8 bytes: per-cell reductions
@@ -72,6 +67,8 @@ struct DevPlan {
 cudaError_t prepare_unit_kernels(DevPlan& P);
 cudaError_t launch_unit_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s);
 cudaError_t launch_unit_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s);
+// FP32 solve of a new right-hand side with the factor launch_unit_solve_f32 left in the workspace.
+cudaError_t launch_unit_resolve_f32(const DevPlan& P, const float* u, float* b, cudaStream_t s);
 cudaError_t launch_unit_solve_compensated(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
                                           cudaStream_t s);
 cudaError_t launch_unit_cable(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
@@ -87,9 +84,11 @@ cudaError_t launch_pk_cable(const DevPlan& P, const double* sv, const double* g,
 cudaError_t launch_pack(const DevPlan& P, int elem_bytes, const void* natural, void* packed, cudaStream_t s);
 cudaError_t launch_unpack(const DevPlan& P, int elem_bytes, const void* packed, void* natural, cudaStream_t s);
 
-// Refinement solve and adjoint gathers (hines_kernels.cu).
-cudaError_t launch_solve_refine(const DevPlan& P, const float* d, const float* u, const float* b, double* x,
-                                int steps, double* relres, cudaStream_t s);
+// FP32 elimination + FP64 residual refinement on the warp-task kernels (refine_kernels.cu).
+cudaError_t launch_unit_refine(const DevPlan& P, const float* d, const float* u, const float* b, double* x, int steps,
+                               double* relres, cudaStream_t s);
+
+// Adjoint gathers and loss terms (hines_kernels.cu).
 cudaError_t launch_grad_du(const DevPlan& P, const double* lam, const double* x, double* gd, double* gu,
                            cudaStream_t s);
 cudaError_t launch_cable_adjoint_step(const DevPlan& P, const double* lam, const double* Vk, const double* Vkm1,

@@ -336,8 +336,12 @@ struct CompModeT {
 // d_i = s_i (1 + theta dt g_i) + sum of a over the edges at i (a = -u),
 // b_i = s_i V_i + s_i dt g_i (E - (1 - theta) V_i).
 // ============================================================================
-template <typename T, bool kCable, bool kPk>
+// kReuse: the elimination of a new right-hand side with the factor a previous
+// solve of the same plan left in the workspace (the reciprocal eliminated
+// diagonal): only b is eliminated (the refinement's correction solves).
+template <typename T, bool kCable, bool kPk, bool kReuse = false>
 struct FactorMode {
+  static_assert(!kReuse || (!kCable && !kPk), "factor reuse: natural layout, plain system");
   static constexpr bool kPacked = kPk;
   struct Args {
     const T* d;
@@ -399,9 +403,10 @@ struct FactorMode {
         cp_async(&sb[q], A.x + fj + t);
       });
     } else if (!kCable) {
+      const T* dsrc = kReuse ? static_cast<const T*>(P.fac) : A.d;
       for_branch_elements(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
         const int q = sidx(lj - 1 - t, jj);
-        cp_async(&sd[q], A.d + fj + t);
+        cp_async(&sd[q], dsrc + fj + t);
         cp_async(&su[q], A.u + fj + t);
         cp_async(&sb[q], A.x + fj + t);
       });
@@ -433,6 +438,34 @@ struct FactorMode {
     if (lane >= n) return;
     const int pos = c0 + lane;
     const int len = m.len;
+    if (kReuse && visit == 0) {  // sd holds the stored reciprocals; eliminate b only
+      T B = sb[Q(0, lane)];
+      for (int i = 0; i < m.nchild; ++i) {
+        const int cp = child_pos(P, m, i);
+        const int loc = cp - pv.c0;
+        const bool local = loc >= 0 && loc < pv.n;
+        B -= local ? cslot[(pv.which * 32 + loc) * 2 + 1] : slot_load(slot + 2 * cp + 1, m);
+      }
+      for (int k = 0; k < len - 1; ++k) {
+        const int q = Q(k, lane);
+        sb[q] = B;
+        const T f = su[q] * sd[q];
+        B = sb[Q(k + 1, lane)] - f * B;
+      }
+      const int q = Q(len - 1, lane);
+      T c1v = T(0);
+      if (m.pcomp >= 0) {
+        sb[q] = B;
+        c1v = su[q] * sd[q] * B;
+      } else {
+        sb[q] = B * sd[q];  // solve root
+      }
+      slot[2 * pos] = T(0);
+      slot[2 * pos + 1] = c1v;
+      cslot[(cur * 32 + lane) * 2] = T(0);
+      cslot[(cur * 32 + lane) * 2 + 1] = c1v;
+      return;
+    }
     if (visit == 0) {
       if (kPk && kCable) {  // own edge to the parent, except at the cell's root compartment
         for (int k = 0; k < len; ++k)
@@ -505,7 +538,7 @@ struct FactorMode {
     }
     for_branch_elements(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
       const int q = sidx(lj - 1 - t, jj);
-      if (visit == 0) fac[fj + t] = sd[q];
+      if (visit == 0 && !kReuse) fac[fj + t] = sd[q];
       A.x[fj + t] = sb[q];
     });
   }
@@ -682,6 +715,7 @@ using PkF64 = FactorMode<double, false, true>;
 using PkF32 = FactorMode<float, false, true>;
 using PkComp = CompModeT<true>;
 using PkCable = FactorMode<double, true, true>;
+using F32Reuse = FactorMode<float, false, false, true>;
 
 }  // namespace
 
@@ -694,6 +728,8 @@ cudaError_t prepare_unit_kernels(DevPlan& P) {
   if (e == cudaSuccess) e = grid_of<PkF32>(P, &P.grid[5]);
   if (e == cudaSuccess) e = grid_of<PkComp>(P, &P.grid[6]);
   if (e == cudaSuccess) e = grid_of<PkCable>(P, &P.grid[7]);
+  int g_reuse = 0;  // same footprint as the FP32 solve
+  if (e == cudaSuccess) e = grid_of<F32Reuse>(P, &g_reuse);
   return e;
 }
 
@@ -739,6 +775,11 @@ cudaError_t launch_pk_cable(const DevPlan& P, const double* sv, const double* g,
                             double E, int theta, bool rhs_from_V, cudaStream_t s) {
   PkCable::Args A{nullptr, u, sv, g, V, dt, E, (double)theta, rhs_from_V};
   return launch_phases<PkCable>(P, A, P.grid[7], s);
+}
+
+cudaError_t launch_unit_resolve_f32(const DevPlan& P, const float* u, float* b, cudaStream_t s) {
+  F32Reuse::Args A{nullptr, u, nullptr, nullptr, b, 0.f, 0.f, 0.f, false};
+  return launch_phases<F32Reuse>(P, A, P.grid[1], s);
 }
 
 }  // namespace hines
