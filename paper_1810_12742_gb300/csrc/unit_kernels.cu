@@ -342,6 +342,15 @@ struct CompModeT {
 template <typename T, bool kCable, bool kPk, bool kReuse = false>
 struct FactorMode {
   static_assert(!kReuse || (!kCable && !kPk), "factor reuse: natural layout, plain system");
+  // the reciprocal eliminated diagonal: FP64 as rcp_t gives it; FP32 with one
+  // more Newton step on the hardware approximation, so that the stored factor
+  // is that of an FP32 elimination to the last bit or so, which the
+  // refinement's re-solves depend on
+  __device__ static T rcp_solve(T x) {
+    T r = rcp_t(x);
+    if (sizeof(T) == 4) r = fma(r, fma(-x, r, T(1)), r);
+    return r;
+  }
   static constexpr bool kPacked = kPk;
   struct Args {
     const T* d;
@@ -481,7 +490,7 @@ struct FactorMode {
       }
       for (int k = 0; k < len - 1; ++k) {
         const T uk = su[Q(k, lane)];
-        const T r = rcp_t(D);
+        const T r = rcp_solve(D);
         sd[Q(k, lane)] = r;
         sb[Q(k, lane)] = B;
         const T f = uk * r;
@@ -490,7 +499,7 @@ struct FactorMode {
         B = sb[Q(k + 1, lane)] - f * B;
       }
       const int k = len - 1;
-      const T r = rcp_t(D);
+      const T r = rcp_solve(D);
       sd[Q(k, lane)] = r;
       T c0v = T(0), c1v = T(0);
       if (m.pcomp >= 0) {
