@@ -406,3 +406,58 @@ def solve_compensated_host(plan: Plan, d, u, b, x):
     solve_compensated(plan, st[0], st[1], st[2], st[3])
     x.copy_(st[3], non_blocking=True)
     return x
+
+
+class HostPipeline:
+    """The compensated solve from host arrays, with the transfers overlapped:
+    the batch is cut into ``pieces`` runs of consecutive cells of about equal
+    size, each with its own plan and device buffers, and per piece the
+    host-to-device copy, the solve and the device-to-host copy run on three
+    streams, so that piece k is solved while piece k+1 arrives and piece k-1
+    leaves.  ``solve_compensated`` takes pinned host tensors in the natural
+    layout of the whole batch and returns when the work is enqueued on the
+    current stream (which waits for all of it)."""
+
+    def __init__(self, ncomp, parent, pieces: int = 8):
+        torch = _torch()
+        nc = np.ascontiguousarray(ncomp, np.int64)
+        pa = np.ascontiguousarray(parent, np.int32)
+        off = np.concatenate(([0], np.cumsum(nc)))
+        total = int(off[-1])
+        pieces = max(1, min(int(pieces), nc.size))
+        # cell boundaries closest to equal compartment counts
+        cuts = np.searchsorted(off, np.linspace(0, total, pieces + 1)[1:-1], side="left")
+        bounds = np.unique(np.concatenate(([0], cuts, [nc.size])))
+        self.parts = []
+        for c0, c1 in zip(bounds[:-1], bounds[1:]):
+            lo, hi = int(off[c0]), int(off[c1])
+            plan = Plan(nc[c0:c1], pa[lo:hi])
+            n = hi - lo
+            bufs = tuple(torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)) + (
+                torch.empty(n, dtype=torch.float64, device="cuda"),)
+            self.parts.append((lo, hi, plan, bufs))
+        self.n_unknowns = total
+        self.streams = [torch.cuda.Stream() for _ in range(3)]
+
+    def solve_compensated(self, d, u, b, x):
+        torch = _torch()
+        cur = torch.cuda.current_stream()
+        s_in, s_run, s_out = self.streams
+        for s in self.streams:
+            s.wait_stream(cur)
+        for lo, hi, plan, (dd, uu, bb, xx) in self.parts:
+            with torch.cuda.stream(s_in):
+                for dst, src in zip((dd, uu, bb), (d, u, b)):
+                    dst.copy_(src[lo:hi], non_blocking=True)
+                ready = torch.cuda.Event()
+                ready.record(s_in)
+            with torch.cuda.stream(s_run):
+                s_run.wait_event(ready)
+                solve_compensated(plan, dd, uu, bb, xx)
+                done = torch.cuda.Event()
+                done.record(s_run)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(done)
+                x[lo:hi].copy_(xx, non_blocking=True)
+        cur.wait_stream(s_out)
+        return x
