@@ -485,11 +485,12 @@ def main():
         cp = I.population(ws, cells=cells, keys=("s", "a", "u", "g", "V0"))
         cs = {k: torch.as_tensor(cp[k]).cuda() for k in ("s", "g", "u", "V0")}
         cable = {"steps_per_graph": args.cable_steps, "algorithmic_bytes_per_compartment": BYTES_CABLE,
-                 "path": "hines_cable_step (theta 1) x steps in one CUDA graph"}
-        for layout in ("natural", "solver"):
+                 "path": "hines_cable_step (theta 1) x steps in one CUDA graph; *_factor_reuse: the first step "
+                         "full, the others hines_cable_step_reuse (constant matrix, a separate variant)"}
+        for layout, reuse in (("natural", False), ("solver", False), ("natural", True), ("solver", True)):
             V = cs["V0"].clone()
             st = R.CableStepper(plan, cs["s"], cs["g"], cs["u"], V, ws.dt, ws.E, 1, steps=args.cable_steps,
-                                layout=layout)
+                                layout=layout, reuse_factor=reuse)
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(stream)
             st.replay()
@@ -503,8 +504,9 @@ def main():
                 ref, _ = oracle.steps_batch(pop["ncomp"][c:c + 1], pop["parent"][sl], cp["s"][sl], cp["g"][sl],
                                             cp["a"][sl], cp["V0"][sl], args.cable_steps, ws.dt, ws.E, 1)
                 err_c = max(err_c, float(np.abs(Vn[sl] - ref).max() / np.abs(ref).max()))
-            cable[layout] = {"ms_per_step": ms, "compartments_per_s": n / (ms * 1e-3), "max_rel_err": err_c,
-                             "hbm_frac": BYTES_CABLE * n / (ms * 1e-3) / 1e9 / load_peaks()[0]}
+            cable[layout + ("_factor_reuse" if reuse else "")] = {
+                "ms_per_step": ms, "compartments_per_s": n / (ms * 1e-3), "max_rel_err": err_c,
+                "hbm_frac": BYTES_CABLE * n / (ms * 1e-3) / 1e9 / load_peaks()[0]}
             del st, V
         del cs, cp
 

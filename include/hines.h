@@ -272,6 +272,25 @@ hines_status hines_cable_solve_packed(hines_plan_t plan, const double *s, const 
                                       double *rhs_inout, double dt, int32_t theta, hines_stream_t stream);
 
 /*
+ * A passive-cable step that re-uses the factor of the last full step.  With
+ * s, g, u, dt and theta unchanged, the step's matrix is the same at every
+ * step (only b depends on V), so after one hines_cable_step (or
+ * hines_cable_step_packed) has left its factor -- the reciprocal eliminated
+ * diagonal -- in the plan's workspace, a step only rebuilds b from V and
+ * eliminates it: no reciprocal, about half the FP64 work.  The result equals
+ * a full step bit for bit.  The caller guarantees that s, g, u, dt and theta
+ * are those of the last full step on this plan, in the same layout, and that
+ * no other call has used the plan's workspace since.  No paper counterpart
+ * (the paper solves each step afresh; factor reuse is the constant-matrix
+ * special case of the passive cable).
+ *   solver_layout  0: natural-layout arrays (n_unknowns); 1: solver layout
+ *                  (n_packed, 16-byte aligned)
+ */
+hines_status hines_cable_step_reuse(hines_plan_t plan, const double *s, const double *g, const double *u,
+                                    double *V_inout, double dt, double E, int32_t theta, int32_t solver_layout,
+                                    hines_stream_t stream);
+
+/*
  * Adjoint gather for x = A^{-1} b with lambda = A^{-1} xbar (A symmetric, so
  * lambda is a second Hines solve):
  *   grad_d[i] = -lambda_i x_i

@@ -385,6 +385,20 @@ hines_status hines_cable_solve_packed(hines_plan_t p, const double* s, const dou
                                          reinterpret_cast<cudaStream_t>(stream)));
 }
 
+hines_status hines_cable_step_reuse(hines_plan_t p, const double* s, const double* g, const double* u,
+                                    double* V_inout, double dt, double E, int32_t theta, int32_t solver_layout,
+                                    hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if (solver_layout != 0 && solver_layout != 1) return HINES_ERR_INVALID_ARG;
+  if (solver_layout ? (!need_pk(p, s) || !need_pk(p, g) || !need_pk(p, u) || !need_pk(p, V_inout))
+                    : (!need(p, s) || !need(p, g) || !need(p, u) || !need(p, V_inout)))
+    return HINES_ERR_INVALID_ARG;
+  if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
+  return launched(hines::launch_unit_cable_reuse(p->dev, s, g, u, V_inout, dt, E, theta, solver_layout != 0,
+                                                 reinterpret_cast<cudaStream_t>(stream)));
+}
+
 hines_status hines_grad_du(hines_plan_t p, const double* lambda, const double* x, double* grad_d, double* grad_u,
                            hines_stream_t stream) {
   hines_status st = check_plan(p);

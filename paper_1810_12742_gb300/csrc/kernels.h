@@ -80,6 +80,9 @@ cudaError_t launch_pk_solve_compensated(const DevPlan& P, const float* d, const 
                                         cudaStream_t s);
 cudaError_t launch_pk_cable(const DevPlan& P, const double* sv, const double* g, const double* u, double* V, double dt,
                             double E, int theta, bool rhs_from_V, cudaStream_t s);
+// Passive-cable step with the factor the last full step left (natural or solver layout).
+cudaError_t launch_unit_cable_reuse(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
+                                    double dt, double E, int theta, bool packed, cudaStream_t s);
 // Natural <-> solver layout permutations (elem_bytes 4 or 8).
 cudaError_t launch_pack(const DevPlan& P, int elem_bytes, const void* natural, void* packed, cudaStream_t s);
 cudaError_t launch_unpack(const DevPlan& P, int elem_bytes, const void* packed, void* natural, cudaStream_t s);

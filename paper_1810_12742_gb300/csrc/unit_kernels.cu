@@ -337,11 +337,11 @@ struct CompModeT {
 // b_i = s_i V_i + s_i dt g_i (E - (1 - theta) V_i).
 // ============================================================================
 // kReuse: the elimination of a new right-hand side with the factor a previous
-// solve of the same plan left in the workspace (the reciprocal eliminated
-// diagonal): only b is eliminated (the refinement's correction solves).
+// solve of the same plan and matrix left in the workspace (the reciprocal
+// eliminated diagonal): only b is eliminated (the refinement's correction
+// solves; passive-cable steps after the first, the matrix being constant).
 template <typename T, bool kCable, bool kPk, bool kReuse = false>
 struct FactorMode {
-  static_assert(!kReuse || (!kCable && !kPk), "factor reuse: natural layout, plain system");
   // the reciprocal eliminated diagonal: FP64 as rcp_t gives it; FP32 with one
   // more Newton step on the hardware approximation, so that the stored factor
   // is that of an FP32 elimination to the last bit or so, which the
@@ -390,17 +390,26 @@ struct FactorMode {
       // the diagonal in compute(), where the cell's root compartment is known
       const long long blk = __shfl_sync(kFull, m.first, 0);
       const int e = chunk_elems(m, n, lane);
+      if (kReuse) {  // the stored factor; only the right-hand side is rebuilt
+        stage_block(sd, static_cast<const T*>(P.fac), blk, e, lane);
+        stage_block(su, A.u, blk, e, lane);
+      }
       for (int i = lane; i < e; i += 32) {
         const long long g = blk + i;
-        const T si = A.s[g], gi = A.g[g], ui = A.u[g], vi = A.x[g];
-        sd[i] = cable_diag(A, si, gi);
-        su[i] = ui;
-        sb[i] = A.rhs_from_V ? cable_rhs(A, si, gi, vi) : vi;
+        const T vi = A.x[g];
+        if (kReuse) {
+          sb[i] = A.rhs_from_V ? cable_rhs(A, A.s[g], A.g[g], vi) : vi;
+        } else {
+          const T si = A.s[g], gi = A.g[g], ui = A.u[g];
+          sd[i] = cable_diag(A, si, gi);
+          su[i] = ui;
+          sb[i] = A.rhs_from_V ? cable_rhs(A, si, gi, vi) : vi;
+        }
       }
     } else if (kPk) {
       const long long blk = __shfl_sync(kFull, m.first, 0);
       const int e = chunk_elems(m, n, lane);
-      stage_block(sd, visit == 1 ? static_cast<const T*>(P.fac) : A.d, blk, e, lane);
+      stage_block(sd, (visit == 1 || kReuse) ? static_cast<const T*>(P.fac) : A.d, blk, e, lane);
       stage_block(su, A.u, blk, e, lane);
       stage_block(sb, static_cast<const T*>(A.x), blk, e, lane);
     } else if (visit == 1) {
@@ -418,6 +427,16 @@ struct FactorMode {
         cp_async(&sd[q], dsrc + fj + t);
         cp_async(&su[q], A.u + fj + t);
         cp_async(&sb[q], A.x + fj + t);
+      });
+    } else if (kReuse) {  // cable, stored factor: only the right-hand side is rebuilt
+      const T* fac = static_cast<const T*>(P.fac);
+      for_branch_elements(m, n, lane, [&](int jj, int t, int lj, long long fj, long long) {
+        const long long i = fj + t;
+        const int q = sidx(lj - 1 - t, jj);
+        cp_async(&sd[q], fac + i);
+        cp_async(&su[q], A.u + i);
+        const T vi = A.x[i];
+        sb[q] = A.rhs_from_V ? cable_rhs(A, A.s[i], A.g[i], vi) : vi;
       });
     } else {
       for_branch_elements<true>(m, n, lane, [&](int jj, int t, int lj, long long fj, long long pc) {
@@ -540,7 +559,7 @@ struct FactorMode {
       const long long blk = __shfl_sync(kFull, m.first, 0);
       const int e = chunk_elems(m, n, lane);
       for (int i = lane; i < e; i += 32) {
-        if (visit == 0) fac[blk + i] = sd[i];
+        if (visit == 0 && !kReuse) fac[blk + i] = sd[i];
         A.x[blk + i] = sb[i];
       }
       return;
@@ -725,6 +744,8 @@ using PkF32 = FactorMode<float, false, true>;
 using PkComp = CompModeT<true>;
 using PkCable = FactorMode<double, true, true>;
 using F32Reuse = FactorMode<float, false, false, true>;
+using CableReuse = FactorMode<double, true, false, true>;
+using PkCableReuse = FactorMode<double, true, true, true>;
 
 }  // namespace
 
@@ -739,6 +760,8 @@ cudaError_t prepare_unit_kernels(DevPlan& P) {
   if (e == cudaSuccess) e = grid_of<PkCable>(P, &P.grid[7]);
   int g_reuse = 0;  // same footprint as the FP32 solve
   if (e == cudaSuccess) e = grid_of<F32Reuse>(P, &g_reuse);
+  if (e == cudaSuccess) e = grid_of<CableReuse>(P, &g_reuse);
+  if (e == cudaSuccess) e = grid_of<PkCableReuse>(P, &g_reuse);
   return e;
 }
 
@@ -789,6 +812,16 @@ cudaError_t launch_pk_cable(const DevPlan& P, const double* sv, const double* g,
 cudaError_t launch_unit_resolve_f32(const DevPlan& P, const float* u, float* b, cudaStream_t s) {
   F32Reuse::Args A{nullptr, u, nullptr, nullptr, b, 0.f, 0.f, 0.f, false};
   return launch_phases<F32Reuse>(P, A, P.grid[1], s);
+}
+
+cudaError_t launch_unit_cable_reuse(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
+                                    double dt, double E, int theta, bool packed, cudaStream_t s) {
+  if (packed) {
+    PkCableReuse::Args A{nullptr, u, sv, g, V, dt, E, (double)theta, true};
+    return launch_phases<PkCableReuse>(P, A, P.grid[7], s);
+  }
+  CableReuse::Args A{nullptr, u, sv, g, V, dt, E, (double)theta, true};
+  return launch_phases<CableReuse>(P, A, P.grid[2], s);
 }
 
 }  // namespace hines

@@ -36,7 +36,7 @@ EXPORTS = [
     "hines_status_string",
     "hines_solve_f64_noalloc",
     "hines_plan_export_packed", "hines_pack", "hines_unpack", "hines_solve_packed", "hines_solve_compensated_packed",
-    "hines_cable_step_packed", "hines_cable_solve_packed",
+    "hines_cable_step_packed", "hines_cable_solve_packed", "hines_cable_step_reuse",
 ]
 
 
@@ -92,6 +92,7 @@ def lib():
             L.hines_solve_compensated_packed.argtypes = [vp, vp, vp, vp, vp, vp]
             L.hines_cable_step_packed.argtypes = [vp, vp, vp, vp, vp, f64, f64, i32, vp]
             L.hines_cable_solve_packed.argtypes = [vp, vp, vp, vp, vp, f64, i32, vp]
+            L.hines_cable_step_reuse.argtypes = [vp, vp, vp, vp, vp, f64, f64, i32, i32, vp]
             L.hines_status_string.argtypes = [i32]
             L.hines_status_string.restype = ctypes.c_char_p
             for name in EXPORTS:
@@ -295,6 +296,19 @@ def cable_step_packed(plan: Plan, s, g, u, V, dt: float, E: float, theta: int = 
     _check(lib().hines_cable_step_packed(plan.handle, _pptr(s, torch.float64, n, "s"), _pptr(g, torch.float64, n, "g"),
                                          _pptr(u, torch.float64, n, "u"), _pptr(V, torch.float64, n, "V"),
                                          float(dt), float(E), int(theta), _stream()), "hines_cable_step_packed")
+    return V
+
+
+def cable_step_reuse(plan: Plan, s, g, u, V, dt: float, E: float, theta: int = 1, solver_layout: bool = False):
+    """hines_cable_step_reuse: a cable step with the factor of the last full
+    step on this plan (same s, g, u, dt, theta and layout); V in place."""
+    torch = _torch()
+    n = plan.n_packed if solver_layout else plan.n_unknowns
+    ptr = _pptr if solver_layout else _dptr
+    _check(lib().hines_cable_step_reuse(plan.handle, ptr(s, torch.float64, n, "s"), ptr(g, torch.float64, n, "g"),
+                                        ptr(u, torch.float64, n, "u"), ptr(V, torch.float64, n, "V"), float(dt),
+                                        float(E), int(theta), int(bool(solver_layout)), _stream()),
+           "hines_cable_step_reuse")
     return V
 
 

@@ -27,31 +27,35 @@ class CableStepper:
     layout "natural": the graph steps the caller's V in place.  layout
     "solver": s, g, u and V are permuted once into the solver layout
     (Section 5) and the graph steps that copy; ``fetch()`` writes the state
-    back into the caller's V."""
+    back into the caller's V.  reuse_factor: every replay makes one full step
+    and then steps that re-use its factor (hines_cable_step_reuse; the
+    passive cable's matrix does not change), with the same results."""
 
     def __init__(self, plan: H.Plan, s, g, u, V, dt: float, E: float, theta: int = 1, steps: int = 1000,
-                 layout: str = "natural"):
+                 layout: str = "natural", reuse_factor: bool = False):
         if layout not in ("natural", "solver"):
             raise ValueError(f"layout: expected 'natural' or 'solver', got {layout!r}")
         self.plan, self.V, self.layout = plan, V, layout
         self.steps = steps
-        if layout == "solver":
+        packed = layout == "solver"
+        if packed:
             self.pk = [H.pack(plan, t) for t in (s, g, u, V)]
-
-            def step(Vt):
-                H.cable_step_packed(plan, self.pk[0], self.pk[1], self.pk[2], Vt, dt, E, theta)
-            state = self.pk[3]
+            s, g, u, state = self.pk
         else:
-            def step(Vt):
-                H.cable_step(plan, s, g, u, Vt, dt, E, theta)
             state = V
+
+        def full(Vt):
+            (H.cable_step_packed if packed else H.cable_step)(plan, s, g, u, Vt, dt, E, theta)
+
+        def reuse(Vt):  # the matrix is constant: the factor of the replay's first step serves the rest
+            H.cable_step_reuse(plan, s, g, u, Vt, dt, E, theta, solver_layout=packed)
         # one eager step on a scratch copy creates the kernels' resources before capture
-        step(state.clone())
+        full(state.clone())
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
-            for _ in range(steps):
-                step(state)
+            for k in range(steps):
+                (reuse if reuse_factor and k > 0 else full)(state)
 
     def replay(self):
         self.graph.replay()

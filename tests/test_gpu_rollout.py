@@ -91,6 +91,36 @@ def test_solver_layout_steps_equal_natural(theta):
     assert torch.equal(b.fetch(), V1)
 
 
+@pytest.mark.parametrize("theta", [0, 1])
+def test_cable_steps_reusing_the_factor_equal_full_steps(theta):
+    """After one full step the passive cable's factor serves later steps
+    (the matrix is constant): bit-identical states, both layouts, eager and
+    in the graph stepper."""
+    w, pop = uneven_subset(24, 2)
+    plan = H.Plan(pop["ncomp"], pop["parent"])
+    s, g, u = dev(pop["s"]), dev(pop["g"]), dev(pop["u"])
+    Vf, Vr = dev(pop["V0"]), dev(pop["V0"])
+    for k in range(6):
+        H.cable_step(plan, s, g, u, Vf, w.dt, w.E, theta)
+    H.cable_step(plan, s, g, u, Vr, w.dt, w.E, theta)
+    for k in range(5):
+        H.cable_step_reuse(plan, s, g, u, Vr, w.dt, w.E, theta)
+    assert torch.equal(Vf, Vr)
+    pk = [H.pack(plan, t) for t in (s, g, u)]
+    Vp = H.pack(plan, dev(pop["V0"]))
+    H.cable_step_packed(plan, *pk, Vp, w.dt, w.E, theta)
+    for k in range(5):
+        H.cable_step_reuse(plan, *pk, Vp, w.dt, w.E, theta, solver_layout=True)
+    assert torch.equal(H.unpack(plan, Vp), Vf)
+    for layout in ("natural", "solver"):
+        V1, V2 = dev(pop["V0"]), dev(pop["V0"])
+        a = R.CableStepper(plan, s, g, u, V1, w.dt, w.E, theta, steps=6, layout=layout)
+        b = R.CableStepper(plan, s, g, u, V2, w.dt, w.E, theta, steps=6, layout=layout, reuse_factor=True)
+        a.replay()
+        b.replay()
+        assert torch.equal(a.fetch(), b.fetch())
+
+
 def _adjoint_case(cells, steps, ce, theta=1):
     w = I.WORKLOADS["adjoint"]
     pop = I.population(w, cells=cells, keys=("s", "a", "u", "g", "V0", "target"))
