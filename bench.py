@@ -267,6 +267,42 @@ def other_configs(torch, H, oracle, stream, max_over_ranks):
         del plan, f32
     out["margin_sweep"] = {"cells": int(sub.size), "max_rel_err": sweep}
 
+    # branching-probability sweep (the Fig. 7.2 experiment, on 16384-cell-shaped
+    # cells): the warp-task FP64 solve against the one-thread-per-cell serial
+    # solve (hines_solve_f64_noalloc, Listing 2 per thread), same data
+    import ctypes
+    import dataclasses
+    base = I.WORKLOADS["fp64_uniform"]
+    sweep_b = {}
+    for ps in (0.3, 0.5, 0.9):
+        wb = dataclasses.replace(base, name=f"fp64_uniform p_split {ps}", n_cells=480,
+                                 classes=(dataclasses.replace(base.classes[0], p_split=ps),))
+        pop = I.population(wb)
+        nb_ = int(pop["offsets"][-1])
+        plan = H.Plan(pop["ncomp"], pop["parent"])
+        d, u, b = (torch.as_tensor(pop[k]).cuda() for k in ("d", "u", "b"))
+        off_d = torch.as_tensor(pop["offsets"]).cuda()
+        par_d = torch.as_tensor(pop["parent"].astype(np.int32)).cuda()
+        x1, x2 = b.clone(), b.clone()
+        vp = ctypes.c_void_p
+
+        def one_thread_per_cell():
+            code = H.lib().hines_solve_f64_noalloc(nb_, int(pop["ncomp"].size), vp(off_d.data_ptr()),
+                                                   vp(par_d.data_ptr()), vp(d.data_ptr()), vp(u.data_ptr()),
+                                                   vp(x2.data_ptr()), vp(stream.cuda_stream))
+            assert code == 0
+        ms_w = max_over_ranks(_timed_ms(torch, stream, lambda: H.solve(plan, d, u, x1), 20))
+        ms_t = max_over_ranks(_timed_ms(torch, stream, one_thread_per_cell, 5))
+        x1.copy_(b)
+        x2.copy_(b)
+        H.solve(plan, d, u, x1)
+        one_thread_per_cell()
+        same = float((x1 - x2).abs().max().item() / x2.abs().max().item())
+        sweep_b[f"{ps:g}"] = {"compartments": nb_, "warp_tasks_ms": ms_w, "one_thread_per_cell_ms": ms_t,
+                              "speedup": ms_t / ms_w, "max_rel_diff": same}
+        del plan
+    out["branching_sweep"] = sweep_b
+
     # adjoint: 256 cells, 200 implicit-Euler steps, checkpoints every 20
     w = I.WORKLOADS["adjoint"]
     pop = I.population(w, keys=("s", "a", "u", "g", "V0", "target"))
