@@ -1,0 +1,53 @@
+"""The plan autotuner: it picks the fastest of its candidate options on a
+synthetic system of the morphology, caches the choice, and the plan it
+returns meets the solve's tolerance against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1810_12742_gb300 import autotune as T
+from paper_1810_12742_gb300 import hines as H
+from tests.test_gpu_packed import uneven_subset
+from tests.test_gpu_parity import cell_rel_err, dev
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tune_picks_the_fastest_and_caches(tmp_path):
+    pop = uneven_subset()
+    cache = str(tmp_path / "tune.json")
+    cands = [dict(pack_compartments=4096), dict(pack_compartments=24576), dict(pack_compartments=24576,
+                                                                              sort_by_length=True)]
+    plan, rep = T.tune_plan(pop["ncomp"], pop["parent"], candidates=cands, reps=2, cache_path=cache)
+    assert not rep["cached"] and rep["options"] in cands
+    assert min(rep["ms"].values()) == rep["ms"][__import__("json").dumps(rep["options"], sort_keys=True)]
+    plan2, rep2 = T.tune_plan(pop["ncomp"], pop["parent"], candidates=cands, cache_path=cache)
+    assert rep2["cached"] and rep2["options"] == rep["options"]
+    f32 = {k: pop[k].astype(np.float32) for k in ("d", "u", "b")}
+    x = H.solve_compensated(plan2, *(dev(f32[k], torch.float32) for k in ("d", "u", "b"))).cpu().numpy()
+    ref = oracle.solve_batch(pop["ncomp"], pop["parent"], *(f32[k].astype(np.float64) for k in ("d", "u", "b")))
+    assert cell_rel_err(x, ref, pop["offsets"]).max() <= 1e-10
+    # the cached options rebuild the tuned plan: the same schedule, the same bits
+    xt = H.solve_compensated(plan, *(dev(f32[k], torch.float32) for k in ("d", "u", "b"))).cpu().numpy()
+    assert np.array_equal(x, xt)
+
+
+def test_synthetic_system_is_diagonally_dominant():
+    pop = uneven_subset()
+    d, u, b = T._system(pop["ncomp"], pop["parent"])
+    plan = H.Plan(pop["ncomp"], pop["parent"])
+    x = b.clone()
+    H.solve(plan, d, u, x)
+    ref = oracle.solve_batch(pop["ncomp"], pop["parent"], d.cpu().numpy(), u.cpu().numpy(), b.cpu().numpy())
+    assert cell_rel_err(x.cpu().numpy(), ref, pop["offsets"]).max() <= 1e-12
+    # strict dominance: d_i exceeds the couplings of row i by s_i >= 0.01
+    off = pop["offsets"]
+    dn, un = d.cpu().numpy(), u.cpu().numpy()
+    row = np.abs(un).copy()
+    par = pop["parent"].astype(np.int64) + np.repeat(off[:-1], pop["ncomp"])
+    nonroot = np.ones(dn.size, bool)
+    nonroot[off[:-1][pop["ncomp"] > 0]] = False
+    row[~nonroot] = 0.0
+    np.add.at(row, par[nonroot], np.abs(un[nonroot]))
+    assert (dn - row >= 0.01 - 1e-12).all()
