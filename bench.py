@@ -224,6 +224,17 @@ def other_configs(torch, H, oracle, stream, max_over_ranks):
     cells = np.arange(pop["ncomp"].size)
     out["fp64_small"] = {"us_per_solve": us, "compartments": int(pop["offsets"][-1]),
                          "max_rel_err": _cell_err(x.cpu().numpy(), oracle_cells(pop, cells), pop["offsets"], cells)}
+    # solver layout, as built and re-rooted at the centres (Section 6): the
+    # critical path of a warp is the depth of its cells
+    for tag, pl in (("solver_layout", plan), ("rerooted", H.Plan(pop["ncomp"], pop["parent"], reroot=True))):
+        dp, up_, xp = H.pack(pl, d), H.pack_coupling(pl, u), H.pack(pl, b)
+        xs = xp.clone()
+        us_t = max_over_ranks(_timed_ms(torch, stream, lambda: H.solve_packed(pl, dp, up_, xs), 200) * 1e3)
+        xs = xp.clone()
+        H.solve_packed(pl, dp, up_, xs)
+        out["fp64_small"][f"us_per_solve_{tag}"] = us_t
+        out["fp64_small"][f"max_rel_err_{tag}"] = _cell_err(H.unpack(pl, xs).cpu().numpy(), oracle_cells(pop, cells),
+                                                            pop["offsets"], cells)
     del plan
 
     # 16384 cells, about 59M compartments, FP64
@@ -511,6 +522,17 @@ def main():
     ms_unpack = timed(lambda: H.unpack(plan, xpk, x), 3)
     del pk, xpk
 
+    # the same, with every cell re-rooted at its centre (Section 6): couplings
+    # packed through the plan's edge map
+    t_rr = time.perf_counter()
+    plan_rr = H.Plan(pop["ncomp"], pop["parent"], reroot=True)
+    plan_rr_s = time.perf_counter() - t_rr
+    pk = {"d": H.pack(plan_rr, f32["d"]), "u": H.pack_coupling(plan_rr, f32["u"]), "b": H.pack(plan_rr, f32["b"])}
+    xpk = torch.empty(plan_rr.n_packed, dtype=torch.float64, device="cuda")
+    ms_rr = timed(lambda: H.solve_compensated_packed(plan_rr, pk["d"], pk["u"], pk["b"], xpk), args.steps)
+    err_rr = max_rel_err(H.unpack(plan_rr, xpk), True)
+    del pk, xpk, plan_rr
+
     # passive-cable time stepping (rebuild of d and b from V fused with the FP64
     # solve), the same trees: K steps captured in one CUDA graph, natural layout
     # and solver layout
@@ -580,7 +602,9 @@ def main():
                           "max_rel_err": err_pk, "n_packed": plan.n_packed,
                           "roofline_frac": BYTES_F32_IN * n / (ms_pk * 1e-3) / 1e9 / peak,
                           "pack_d_u_b_ms": ms_pack, "unpack_x_ms": ms_unpack,
-                          "path": "hines_solve_compensated_packed on d, u, b, x kept in the solver layout"},
+                          "path": "hines_solve_compensated_packed on d, u, b, x kept in the solver layout",
+                          "rerooted": {"ms_per_solve": ms_rr, "max_rel_err": err_rr, "plan_create_s": plan_rr_s,
+                                       "path": "the same on a plan with every cell re-rooted at its centre"}},
         "cable_steps": cable,
         "configs": configs,
         "fp32_refine": {"value": n / (ms_ref * 1e-3), "unit": "compartments/s", "ms_per_solve": ms_ref,

@@ -75,7 +75,14 @@ typedef struct {
                                 (0: 24576, or total / 2048 for smaller batches, so that they still
                                 give one task per warp); -1: Section 4's rule instead (a unit joins a task
                                 while every level of the task holds at most 32 branches) */
-  int32_t reserved[3];     /* must be zero */
+  int32_t reroot;          /* 1: re-root every cell at its centre (Section 6, balancing the
+                              dependency tree; see hines_plan_export_reroot).  Such a plan
+                              numbers compartments its own way and takes solver-layout
+                              arrays only: the natural-layout entry points return
+                              HINES_ERR_INVALID_ARG, and hines_pack / hines_pack_coupling /
+                              hines_unpack map straight between the caller's numbering
+                              and its solver layout */
+  int32_t reserved[2];     /* must be zero */
 } hines_plan_opts;
 
 /* Plan summary. */
@@ -170,18 +177,48 @@ hines_status hines_plan_export_tasks(hines_plan_t plan, int64_t *branch_task, in
  * 16-byte aligned.
  *
  * hines_plan_export_packed: host int64[n_packed], the natural-layout index
- * held by each slot, -1 for a padding slot.
+ * held by each slot, -1 for a padding slot (for a re-rooted plan: the index in
+ * the caller's numbering).
  */
 hines_status hines_plan_export_packed(hines_plan_t plan, int64_t *slot_natural);
+
+/*
+ * The re-rooting of a plan created with opts.reroot = 1 (Section 6: a new root
+ * that minimises the depth of each cell's compartment tree, then a renumbering
+ * that keeps every branch on consecutive indices).  Per cell the new root is
+ * the centre of the tree: the compartment whose largest distance, in edges, to
+ * any other compartment is smallest (the smaller index when two tie).  The
+ * renumbering visits branches breadth first from the root branch, each branch
+ * proximal to distal, the children of a compartment in ascending caller index.
+ * Host arrays, global indices in the caller's natural layout:
+ *   parent[n_unknowns]  int32, cell-local parent arrays of the re-rooted cells
+ *                       (the morphology that hines_plan_export describes)
+ *   perm[n_unknowns]    caller's index of each re-rooted compartment
+ *   edge[n_unknowns]    caller's index at which the coupling between a
+ *                       re-rooted compartment and its new parent is stored,
+ *                       -1 at a root
+ *   centre[n_cells]     int32, cell-local caller's index of each new root
+ * HINES_ERR_INVALID_ARG for a plan that is not re-rooted.
+ */
+hines_status hines_plan_export_reroot(hines_plan_t plan, int32_t *parent, int64_t *perm, int64_t *edge,
+                                      int32_t *centre);
 
 /*
  * Permute one array between the layouts (device arrays; elem_bytes 4 or 8).
  * hines_pack writes every slot of packed[n_packed] (padding slots: zero) from
  * natural[n_unknowns]; hines_unpack writes natural[n_unknowns] from the
  * non-padding slots of packed.  Stream-ordered.
+ *
+ * hines_pack_coupling packs an array of couplings u (u[i] = A[i, p(i)], stored
+ * at the child end of its edge).  For a plan that is not re-rooted it equals
+ * hines_pack.  For a re-rooted plan the edges between a cell's old and new
+ * root change direction, so each slot takes the coupling of the edge between
+ * its compartment and that compartment's new parent (zero at a new root).
  */
 hines_status hines_pack(hines_plan_t plan, int32_t elem_bytes, const void *natural, void *packed,
                         hines_stream_t stream);
+hines_status hines_pack_coupling(hines_plan_t plan, int32_t elem_bytes, const void *natural, void *packed,
+                                 hines_stream_t stream);
 hines_status hines_unpack(hines_plan_t plan, int32_t elem_bytes, const void *packed, void *natural,
                           hines_stream_t stream);
 

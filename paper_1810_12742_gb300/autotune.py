@@ -2,8 +2,9 @@
 
 The planner's free choices -- how many compartments a warp task holds, whether
 ready branches of equal depth are taken longest first, whether long branches
-are split at their level's mean (Section 6) -- change the schedule, and with it
-only the order in which children's contributions are added to a parent.  Which
+are split at their level's mean, whether cells are re-rooted at their centres
+(both Section 6) -- change the schedule, and with it only the order in which
+the elimination adds contributions into a compartment.  Which
 is fastest depends on the batch (its size classes, depth, branching) and on the
 solve, so ``tune_plan`` times each candidate on a synthetic diagonally dominant
 system of the same morphology and returns the fastest plan.  The choice is
@@ -26,6 +27,11 @@ DEFAULT_CANDIDATES = (
     dict(pack_compartments=32768),
     dict(pack_compartments=24576, sort_by_length=True),
     dict(pack_compartments=24576, split_branches=True),
+)
+# re-rooted plans (Section 6) take solver-layout arrays only
+SOLVER_LAYOUT_CANDIDATES = (
+    dict(pack_compartments=24576, reroot=True),
+    dict(pack_compartments=32768, reroot=True),
 )
 
 
@@ -65,14 +71,14 @@ def _timer(solve, layout, plan, d, u, b):
     if solve == "compensated":
         d32, u32, b32 = (t.float() for t in (d, u, b))
         if layout == "solver":
-            pd, pu, pb = (H.pack(plan, t) for t in (d32, u32, b32))
+            pd, pu, pb = H.pack(plan, d32), H.pack_coupling(plan, u32), H.pack(plan, b32)
             px = torch.empty(plan.n_packed, dtype=torch.float64, device="cuda")
             return lambda: H.solve_compensated_packed(plan, pd, pu, pb, px)
         x = torch.empty(plan.n_unknowns, dtype=torch.float64, device="cuda")
         return lambda: H.solve_compensated(plan, d32, u32, b32, x)
     if solve == "f64":
         if layout == "solver":
-            pd, pu, pb = (H.pack(plan, t) for t in (d, u, b))
+            pd, pu, pb = H.pack(plan, d), H.pack_coupling(plan, u), H.pack(plan, b)
             return lambda: H.solve_packed(plan, pd, pu, pb)
         x = b.clone()
         return lambda: H.solve(plan, d, u, x)
@@ -86,7 +92,11 @@ def tune_plan(ncomp, parent, solve: str = "compensated", layout: str = "natural"
     "cached"}.  A plan rebuilt from cached options schedules exactly as the
     tuned one did."""
     import torch
-    candidates = list(candidates or DEFAULT_CANDIDATES)
+    if candidates is None:
+        candidates = DEFAULT_CANDIDATES + (SOLVER_LAYOUT_CANDIDATES if layout == "solver" else ())
+    candidates = list(candidates)
+    if layout != "solver" and any(c.get("reroot") for c in candidates):
+        raise ValueError("re-rooted plans take the solver layout only")
     key = _key(ncomp, parent, solve, layout)
     cache = {}
     if cache_path and os.path.exists(cache_path):

@@ -10,12 +10,16 @@
 #include "../../include/hines.h"
 #include "kernels.h"
 #include "plan.h"
+#include "reroot.h"
 
 struct hines_plan_s {
   hines::HostPlan host;
   hines::DevPlan dev;
   int device = -1;
   bool host_only = false;
+  bool rerooted = false;         // cells re-rooted at their centres (Section 6)
+  hines::RerootMap rr;           // re-rooted numbering -> caller's numbering
+  std::vector<int64_t> pk_edge;  // [n_packed] caller's index of each slot's coupling (re-rooted plans)
   void* meta = nullptr;
   void* work = nullptr;
   int64_t meta_bytes = 0;
@@ -68,6 +72,7 @@ hines_status upload(hines_plan_t p) {
       {tmeta.data(), tmeta.size() * sizeof(hines::BrMetaT), (const void**)&D.tmeta},
       {pkm.data(), pkm.size() * 8, (const void**)&D.pk_meta},
       {H.pk_perm.data(), H.pk_perm.size() * 8, (const void**)&D.pk_perm},
+      {p->pk_edge.data(), p->pk_edge.size() * 8, (const void**)&D.pk_edge},
       {H.task_nlvl.data(), H.task_nlvl.size() * 4, (const void**)&D.task_nlvl},
       {H.task_lvl_off.data(), H.task_lvl_off.size() * 8, (const void**)&D.task_lvl_off},
       {H.tlvl_ptr.data(), H.tlvl_ptr.size() * 4, (const void**)&D.tlvl_ptr},
@@ -103,6 +108,7 @@ hines_status upload(hines_plan_t p) {
     *it.dst = base + off;
     off += align256(it.bytes > 0 ? it.bytes : 1);
   }
+  if (!p->rerooted) D.pk_edge = D.pk_perm;  // a coupling sits at its child compartment
   const size_t n = (size_t)H.n_unknowns, nb = H.br_first.size(), nc = (size_t)H.n_cells;
   // the factor is indexed by natural or solver-layout position
   const size_t fac_b = align256(std::max(n, (size_t)H.n_packed) * 8 + 8), cd_b = align256(nb * 16 + 16),
@@ -149,6 +155,14 @@ hines_status check_plan(hines_plan_t p) {
   return HINES_OK;
 }
 
+// Entry points that take natural-layout arrays: a re-rooted plan numbers the
+// compartments differently from the caller, so it accepts the solver layout only.
+hines_status check_natural(hines_plan_t p) {
+  const hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  return p->rerooted ? HINES_ERR_INVALID_ARG : HINES_OK;
+}
+
 hines_status launched(cudaError_t e) { return e == cudaSuccess ? HINES_OK : HINES_ERR_CUDA; }
 
 bool need(hines_plan_t p, const void* a) { return a != nullptr || p->host.n_unknowns == 0; }
@@ -164,7 +178,7 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
   hines_plan_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 2; ++k)
     if (o.reserved[k] != 0) return HINES_ERR_INVALID_ARG;
   if (o.pack_compartments < -1) return HINES_ERR_INVALID_ARG;
   if (o.cta_threads == 0) o.cta_threads = 256;
@@ -173,8 +187,22 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
   if (!p) return HINES_ERR_OOM;
   int rc;
   try {
-    rc = hines::build_host_plan(n_cells, ncomp, parent, o.split_branches, o.sort_by_length, o.pack_compartments,
-                                p->host);
+    p->rerooted = o.reroot != 0;
+    rc = p->rerooted ? hines::reroot_batch(n_cells, ncomp, parent, p->rr) : HINES_OK;
+    if (rc == HINES_OK)
+      rc = hines::build_host_plan(n_cells, ncomp, p->rerooted ? p->rr.parent.data() : parent, o.split_branches,
+                                  o.sort_by_length, o.pack_compartments, p->host);
+    if (rc == HINES_OK && p->rerooted) {
+      // the solver layout maps straight to the caller's numbering: node arrays
+      // through the renumbering, couplings through the edge map
+      std::vector<int64_t>& perm = p->host.pk_perm;
+      p->pk_edge.assign(perm.size(), -1);
+      for (size_t k = 0; k < perm.size(); ++k) {
+        if (perm[k] < 0) continue;
+        p->pk_edge[k] = p->rr.edge[(size_t)perm[k]];
+        perm[k] = p->rr.perm[(size_t)perm[k]];
+      }
+    }
   } catch (const std::bad_alloc&) {
     rc = HINES_ERR_OOM;
   }
@@ -265,7 +293,7 @@ hines_status hines_plan_export_tasks(hines_plan_t p, int64_t* branch_task, int64
 
 hines_status hines_solve(hines_plan_t p, int32_t dtype, const void* d, const void* u, void* b_inout,
                          hines_stream_t stream) {
-  hines_status st = check_plan(p);
+  hines_status st = check_natural(p);
   if (st != HINES_OK) return st;
   if (!need(p, d) || !need(p, u) || !need(p, b_inout)) return HINES_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -278,7 +306,7 @@ hines_status hines_solve(hines_plan_t p, int32_t dtype, const void* d, const voi
 
 hines_status hines_solve_compensated(hines_plan_t p, const float* d, const float* u, const float* b, double* x_out,
                                      hines_stream_t stream) {
-  hines_status st = check_plan(p);
+  hines_status st = check_natural(p);
   if (st != HINES_OK) return st;
   if (!need(p, d) || !need(p, u) || !need(p, b) || !need(p, x_out)) return HINES_ERR_INVALID_ARG;
   return launched(
@@ -303,6 +331,28 @@ hines_status hines_pack(hines_plan_t p, int32_t elem_bytes, const void* natural,
   if (st != HINES_OK) return st;
   if ((elem_bytes != 4 && elem_bytes != 8) || !need(p, natural) || !need_pk(p, packed)) return HINES_ERR_INVALID_ARG;
   return launched(hines::launch_pack(p->dev, elem_bytes, natural, packed, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+hines_status hines_pack_coupling(hines_plan_t p, int32_t elem_bytes, const void* natural, void* packed,
+                                 hines_stream_t stream) {
+  hines_status st = check_plan(p);
+  if (st != HINES_OK) return st;
+  if ((elem_bytes != 4 && elem_bytes != 8) || !need(p, natural) || !need_pk(p, packed)) return HINES_ERR_INVALID_ARG;
+  return launched(
+      hines::launch_pack(p->dev, elem_bytes, natural, packed, reinterpret_cast<cudaStream_t>(stream), true));
+}
+
+hines_status hines_plan_export_reroot(hines_plan_t p, int32_t* parent, int64_t* perm, int64_t* edge,
+                                      int32_t* centre) {
+  if (!p || !p->rerooted) return HINES_ERR_INVALID_ARG;
+  const size_t n = p->rr.perm.size(), nc = p->rr.centre.size();
+  if (n > 0 && (!parent || !perm || !edge)) return HINES_ERR_INVALID_ARG;
+  if (nc > 0 && !centre) return HINES_ERR_INVALID_ARG;
+  std::memcpy(parent, p->rr.parent.data(), n * sizeof(int32_t));
+  std::memcpy(perm, p->rr.perm.data(), n * sizeof(int64_t));
+  std::memcpy(edge, p->rr.edge.data(), n * sizeof(int64_t));
+  std::memcpy(centre, p->rr.centre.data(), nc * sizeof(int32_t));
+  return HINES_OK;
 }
 
 hines_status hines_unpack(hines_plan_t p, int32_t elem_bytes, const void* packed, void* natural,
@@ -337,7 +387,7 @@ hines_status hines_solve_compensated_packed(hines_plan_t p, const float* d, cons
 
 hines_status hines_solve_refine(hines_plan_t p, const float* d, const float* u, const float* b, double* x_out,
                                 int32_t refine_steps, double* cell_relres, hines_stream_t stream) {
-  hines_status st = check_plan(p);
+  hines_status st = check_natural(p);
   if (st != HINES_OK) return st;
   if (!need(p, d) || !need(p, u) || !need(p, b) || !need(p, x_out)) return HINES_ERR_INVALID_ARG;
   if (refine_steps < 0 || refine_steps > 4) return HINES_ERR_INVALID_ARG;
@@ -347,7 +397,7 @@ hines_status hines_solve_refine(hines_plan_t p, const float* d, const float* u, 
 
 hines_status hines_cable_step(hines_plan_t p, const double* s, const double* g, const double* u, double* V_inout,
                               double dt, double E, int32_t theta, hines_stream_t stream) {
-  hines_status st = check_plan(p);
+  hines_status st = check_natural(p);
   if (st != HINES_OK) return st;
   if (!need(p, s) || !need(p, g) || !need(p, u) || !need(p, V_inout)) return HINES_ERR_INVALID_ARG;
   if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
@@ -357,7 +407,7 @@ hines_status hines_cable_step(hines_plan_t p, const double* s, const double* g, 
 
 hines_status hines_cable_solve(hines_plan_t p, const double* s, const double* g, const double* u, double* rhs_inout,
                                double dt, int32_t theta, hines_stream_t stream) {
-  hines_status st = check_plan(p);
+  hines_status st = check_natural(p);
   if (st != HINES_OK) return st;
   if (!need(p, s) || !need(p, g) || !need(p, u) || !need(p, rhs_inout)) return HINES_ERR_INVALID_ARG;
   if (theta != 0 && theta != 1) return HINES_ERR_INVALID_ARG;
@@ -391,6 +441,7 @@ hines_status hines_cable_step_reuse(hines_plan_t p, const double* s, const doubl
   hines_status st = check_plan(p);
   if (st != HINES_OK) return st;
   if (solver_layout != 0 && solver_layout != 1) return HINES_ERR_INVALID_ARG;
+  if (!solver_layout && p->rerooted) return HINES_ERR_INVALID_ARG;
   if (solver_layout ? (!need_pk(p, s) || !need_pk(p, g) || !need_pk(p, u) || !need_pk(p, V_inout))
                     : (!need(p, s) || !need(p, g) || !need(p, u) || !need(p, V_inout)))
     return HINES_ERR_INVALID_ARG;
@@ -401,7 +452,7 @@ hines_status hines_cable_step_reuse(hines_plan_t p, const double* s, const doubl
 
 hines_status hines_grad_du(hines_plan_t p, const double* lambda, const double* x, double* grad_d, double* grad_u,
                            hines_stream_t stream) {
-  hines_status st = check_plan(p);
+  hines_status st = check_natural(p);
   if (st != HINES_OK) return st;
   if (!need(p, lambda) || !need(p, x) || !need(p, grad_d) || !need(p, grad_u)) return HINES_ERR_INVALID_ARG;
   return launched(hines::launch_grad_du(p->dev, lambda, x, grad_d, grad_u, reinterpret_cast<cudaStream_t>(stream)));
@@ -411,7 +462,7 @@ hines_status hines_cable_adjoint_step(hines_plan_t p, const double* lambda, cons
                                       const double* s, const double* g, const double* target, double dt, double E,
                                       int32_t theta, int32_t add_loss_term, double* grad_g, double* grad_a,
                                       double* vbar_out, hines_stream_t stream) {
-  hines_status st = check_plan(p);
+  hines_status st = check_natural(p);
   if (st != HINES_OK) return st;
   if (!need(p, lambda) || !need(p, V_k) || !need(p, V_km1) || !need(p, s) || !need(p, g) || !need(p, grad_g) ||
       !need(p, grad_a) || !need(p, vbar_out))
@@ -425,7 +476,7 @@ hines_status hines_cable_adjoint_step(hines_plan_t p, const double* lambda, cons
 
 hines_status hines_cable_loss_seed(hines_plan_t p, const double* V, const double* target, double* vbar,
                                    hines_stream_t stream) {
-  hines_status st = check_plan(p);
+  hines_status st = check_natural(p);
   if (st != HINES_OK) return st;
   if (!need(p, V) || !need(p, vbar) || (!target && p->host.n_cells > 0)) return HINES_ERR_INVALID_ARG;
   return launched(hines::launch_cable_loss_seed(p->dev, V, target, vbar, reinterpret_cast<cudaStream_t>(stream)));
@@ -433,7 +484,7 @@ hines_status hines_cable_loss_seed(hines_plan_t p, const double* V, const double
 
 hines_status hines_cable_loss_accumulate(hines_plan_t p, const double* V, const double* target, double* loss_cells,
                                          hines_stream_t stream) {
-  hines_status st = check_plan(p);
+  hines_status st = check_natural(p);
   if (st != HINES_OK) return st;
   if (!need(p, V) || ((!target || !loss_cells) && p->host.n_cells > 0)) return HINES_ERR_INVALID_ARG;
   return launched(

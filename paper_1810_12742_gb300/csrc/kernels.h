@@ -50,6 +50,7 @@ struct DevPlan {
   int64_t n_packed = 0;
   const longlong2* pk_meta = nullptr;     // [nb] per position: (chunk block offset, parent's solver-layout index)
   const int64_t* pk_perm = nullptr;       // [n_packed] natural index of each solver-layout slot, -1 for padding
+  const int64_t* pk_edge = nullptr;       // [n_packed] natural index of each slot's coupling (pk_perm unless re-rooted)
   int32_t grid[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // persistent grid size per kernel kind
   // workspace
   void* fac = nullptr;    // 8 bytes per natural or solver-layout slot: factor (FP64 / FP32 solves), FP32 working
@@ -84,7 +85,9 @@ cudaError_t launch_pk_cable(const DevPlan& P, const double* sv, const double* g,
 cudaError_t launch_unit_cable_reuse(const DevPlan& P, const double* sv, const double* g, const double* u, double* V,
                                     double dt, double E, int theta, bool packed, cudaStream_t s);
 // Natural <-> solver layout permutations (elem_bytes 4 or 8).
-cudaError_t launch_pack(const DevPlan& P, int elem_bytes, const void* natural, void* packed, cudaStream_t s);
+// coupling: gather through pk_edge (coupling arrays of a re-rooted plan) instead of pk_perm
+cudaError_t launch_pack(const DevPlan& P, int elem_bytes, const void* natural, void* packed, cudaStream_t s,
+                        bool coupling = false);
 cudaError_t launch_unpack(const DevPlan& P, int elem_bytes, const void* packed, void* natural, cudaStream_t s);
 
 // FP32 elimination + FP64 residual refinement on the warp-task kernels (refine_kernels.cu).

@@ -37,13 +37,15 @@ int blocks_for(int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_pack(const DevPlan& P, int elem_bytes, const void* natural, void* packed, cudaStream_t s) {
+cudaError_t launch_pack(const DevPlan& P, int elem_bytes, const void* natural, void* packed, cudaStream_t s,
+                        bool coupling) {
   if (P.n_packed == 0) return cudaSuccess;
+  const int64_t* perm = coupling ? P.pk_edge : P.pk_perm;
   if (elem_bytes == 8)
-    k_pack<uint64_t><<<blocks_for(P.n_packed), 256, 0, s>>>(P.pk_perm, P.n_packed, (const uint64_t*)natural,
+    k_pack<uint64_t><<<blocks_for(P.n_packed), 256, 0, s>>>(perm, P.n_packed, (const uint64_t*)natural,
                                                              (uint64_t*)packed);
   else
-    k_pack<uint32_t><<<blocks_for(P.n_packed), 256, 0, s>>>(P.pk_perm, P.n_packed, (const uint32_t*)natural,
+    k_pack<uint32_t><<<blocks_for(P.n_packed), 256, 0, s>>>(perm, P.n_packed, (const uint32_t*)natural,
                                                              (uint32_t*)packed);
   return cudaGetLastError();
 }

@@ -37,6 +37,7 @@ EXPORTS = [
     "hines_solve_f64_noalloc",
     "hines_plan_export_packed", "hines_pack", "hines_unpack", "hines_solve_packed", "hines_solve_compensated_packed",
     "hines_cable_step_packed", "hines_cable_solve_packed", "hines_cable_step_reuse",
+    "hines_pack_coupling", "hines_plan_export_reroot",
 ]
 
 
@@ -49,7 +50,7 @@ class HinesError(RuntimeError):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("host_only", ctypes.c_int32), ("split_branches", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
                 ("sort_by_length", ctypes.c_int32), ("pack_compartments", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("reroot", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -88,6 +89,8 @@ def lib():
             L.hines_plan_export_packed.argtypes = [vp, vp]
             L.hines_pack.argtypes = [vp, i32, vp, vp, vp]
             L.hines_unpack.argtypes = [vp, i32, vp, vp, vp]
+            L.hines_pack_coupling.argtypes = [vp, i32, vp, vp, vp]
+            L.hines_plan_export_reroot.argtypes = [vp, vp, vp, vp, vp]
             L.hines_solve_packed.argtypes = [vp, i32, vp, vp, vp, vp]
             L.hines_solve_compensated_packed.argtypes = [vp, vp, vp, vp, vp, vp]
             L.hines_cable_step_packed.argtypes = [vp, vp, vp, vp, vp, f64, f64, i32, vp]
@@ -120,15 +123,17 @@ class Plan:
 
     ncomp: compartments per cell; parent: the cells' parent arrays (cell-local,
     p[0] = -1, p[i] < i), concatenated.  host_only builds the schedule without
-    touching the GPU (for inspection)."""
+    touching the GPU (for inspection).  reroot re-roots every cell at its
+    centre (Section 6); such a plan takes solver-layout arrays only (pack node
+    arrays with ``pack``, couplings with ``pack_coupling``)."""
 
     def __init__(self, ncomp, parent, split_branches: bool = False, host_only: bool = False, cta_threads: int = 0,
-                 sort_by_length: bool = False, pack_compartments: int = 0):
+                 sort_by_length: bool = False, pack_compartments: int = 0, reroot: bool = False):
         self._h = ctypes.c_void_p()
         nc = np.ascontiguousarray(ncomp, np.int32)
         pa = np.ascontiguousarray(parent, np.int32)
         opts = PlanOpts(int(host_only), int(split_branches), int(cta_threads), int(sort_by_length),
-                        int(pack_compartments))
+                        int(pack_compartments), int(reroot))
         _check(lib().hines_plan_create(ctypes.byref(self._h), nc.size, _np_ptr(nc), _np_ptr(pa), ctypes.byref(opts)),
                "hines_plan_create")
         info = PlanInfo()
@@ -142,6 +147,7 @@ class Plan:
         self.metadata_bytes = info.metadata_bytes
         self.n_packed = info.n_packed
         self.host_only = host_only
+        self.rerooted = bool(reroot)
         off = np.empty(self.n_cells + 1, np.int64)
         _check(lib().hines_plan_layout(self._h, _np_ptr(off)), "hines_plan_layout")
         self.offsets = off
@@ -168,6 +174,17 @@ class Plan:
         """Natural index held by each solver-layout slot (-1: padding)."""
         out = np.empty(self.n_packed, np.int64)
         _check(lib().hines_plan_export_packed(self._h, _np_ptr(out)), "hines_plan_export_packed")
+        return out
+
+    def export_reroot(self) -> dict:
+        """The re-rooting of a plan made with reroot=True: parent (re-rooted
+        cell-local parent arrays), perm and edge (caller's index of each
+        re-rooted compartment and of its coupling, -1 at a root), centre."""
+        out = {"parent": np.empty(self.n_unknowns, np.int32), "perm": np.empty(self.n_unknowns, np.int64),
+               "edge": np.empty(self.n_unknowns, np.int64), "centre": np.empty(self.n_cells, np.int32)}
+        _check(lib().hines_plan_export_reroot(self._h, *(_np_ptr(out[k]) for k in ("parent", "perm", "edge",
+                                                                                   "centre"))),
+               "hines_plan_export_reroot")
         return out
 
     def status(self) -> int:
@@ -251,6 +268,19 @@ def pack(plan: Plan, natural, packed=None):
     eb = natural.element_size()
     _check(lib().hines_pack(plan.handle, eb, _dptr(natural, natural.dtype, plan.n_unknowns, "natural"),
                             _pptr(packed, natural.dtype, plan.n_packed, "packed"), _stream()), "hines_pack")
+    return packed
+
+
+def pack_coupling(plan: Plan, natural, packed=None):
+    """Natural-layout coupling array u -> solver layout (hines_pack_coupling:
+    through the edge map on a re-rooted plan, else the same as pack)."""
+    torch = _torch()
+    if packed is None:
+        packed = torch.empty(plan.n_packed, dtype=natural.dtype, device=natural.device)
+    eb = natural.element_size()
+    _check(lib().hines_pack_coupling(plan.handle, eb, _dptr(natural, natural.dtype, plan.n_unknowns, "natural"),
+                                     _pptr(packed, natural.dtype, plan.n_packed, "packed"), _stream()),
+           "hines_pack_coupling")
     return packed
 
 

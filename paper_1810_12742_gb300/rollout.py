@@ -39,7 +39,7 @@ class CableStepper:
         self.steps = steps
         packed = layout == "solver"
         if packed:
-            self.pk = [H.pack(plan, t) for t in (s, g, u, V)]
+            self.pk = [H.pack(plan, s), H.pack(plan, g), H.pack_coupling(plan, u), H.pack(plan, V)]
             s, g, u, state = self.pk
         else:
             state = V
