@@ -13,7 +13,8 @@ the 1.8 GB solution) exceed L2, so no flush is needed.
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
 Under torchrun (N > 1) every rank solves its own replica of the population
-(weak scaling, no collective on the data path); rank 0 prints the line.
+(weak scaling, no collective on the data path); with --shard the ranks split
+the population's cells instead (strong scaling).  Rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -53,6 +54,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-pieces", type=int, default=8,
                     help="cell ranges the end-to-end run pipelines its transfers over")
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun, split the population's cells over the ranks (longest-processing-time "
+                         "rule on compartments; strong scaling) instead of a replica per rank (weak scaling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (64-cell, 16384-cell, margin sweep, adjoint)")
@@ -353,14 +357,25 @@ def main():
     from paper_1810_12742_gb300 import inputs as I
     w = I.WORKLOADS[args.workload]
     cells = np.arange(args.cells) if args.cells else None
+    sharded = args.shard and world > 1 and args.impl != "reference"
+    if sharded:  # every rank computes the same split; nothing is exchanged
+        from paper_1810_12742_gb300 import shard as S
+        nc_all, _ = I.population_trees(w, cells)
+        part = S.lpt_partition(nc_all, world)[rank]
+        cells = part if cells is None else cells[part]
     pop = I.population(w, cells=cells, margin=args.margin)
     n = int(pop["offsets"][-1])
+    n_job = int(nc_all.sum()) if sharded else n * world  # compartments the whole job solves per step
     widen = True
     config = {"workload": w.name, "cells": int(pop["ncomp"].size), "compartments": n,
               "leak_margin": args.margin, "path": "hines_solve_compensated: FP32 d, u, b -> FP64 x, "
               "double-float elimination from FP32 error-free transformations",
               "l2": "inputs and solution (4.6 GB at full size) exceed L2; no flush",
-              "seed": f"numpy PCG64 per cell, base {I.SEED_BASE}"}
+              "seed": f"numpy PCG64 per cell, base {I.SEED_BASE}",
+              "parallelism": (f"cells split over {world} ranks (longest-processing-time rule on compartments)"
+                              if sharded else f"{world} replica(s), one per GPU, no collective on the data path")}
+    if sharded:
+        config["job_compartments"] = n_job
     metric = "compartments solved/sec per GB300 and % of HBM roofline, FP32+refine vs FP64"
 
     if args.impl == "reference":
@@ -452,7 +467,7 @@ def main():
     barrier()
     ms_total = max_over_ranks(e0.elapsed_time(e1))
     ms_step = ms_total / args.steps
-    value = job_value(n, args.steps, world, ms_total)
+    value = n_job * args.steps / (ms_total * 1e-3) if sharded else job_value(n, args.steps, world, ms_total)
     status = plan.status()
 
     # parity on sampled cells against the oracle
@@ -586,8 +601,9 @@ def main():
     tr_pk = traffic_record("k_units<CompModeT<solver layout>>")
     line = {
         "metric": metric, "value": value, "unit": "compartments/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config,
         "max_rel_err": err, "status": status,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None if tr is None else tr * n,
@@ -610,8 +626,8 @@ def main():
         "fp32_refine": {"value": n / (ms_ref * 1e-3), "unit": "compartments/s", "ms_per_solve": ms_ref,
                         "refine_steps": args.refine_steps, "max_rel_err": err_ref,
                         "roofline_frac": BYTES_F32_IN * n / (ms_ref * 1e-3) / 1e9 / peak},
-        "e2e": {"value": n / (e2e_ms * 1e-3), "unit": "compartments/s",
-                "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 8 * n, "max_rel_err": e2e_err,
+        "e2e": {"value": n_job / (e2e_ms * 1e-3), "unit": "compartments/s",
+                "h2d_bytes_per_step": 12 * n_job, "d2h_bytes_per_step": 8 * n_job, "max_rel_err": e2e_err,
                 "path": f"HostPipeline.solve_compensated: pinned host arrays, {args.e2e_pieces} pieces, "
                         "transfers overlapped with the solves"},
         "clocks": clk.summary(),
