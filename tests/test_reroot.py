@@ -209,3 +209,14 @@ def test_export_reroot_needs_a_rerooted_plan():
         H.Plan(ncomp, parent, host_only=True).export_reroot()
     with pytest.raises(H.HinesError):  # validation still applies
         H.Plan(ncomp, np.array([-1, 2, 0], np.int32), host_only=True, reroot=True)
+
+
+def test_empty_cells_and_batches():
+    plan = H.Plan(np.zeros(0, np.int32), np.zeros(0, np.int32), host_only=True, reroot=True)
+    assert plan.n_unknowns == 0 and plan.export_reroot()["perm"].size == 0
+    ncomp = np.array([0, 1, 0, 3], np.int32)
+    parent = np.array([-1, -1, 0, 1], np.int32)
+    got = _compare(ncomp, parent)
+    assert got["perm"].tolist() == [0, 2, 1, 3]  # the chain 1-2-3 re-rooted at its middle
+    assert got["edge"].tolist() == [-1, -1, 2, 3]
+    assert got["parent"].tolist() == [-1, -1, 0, 0]
