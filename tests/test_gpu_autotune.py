@@ -51,3 +51,19 @@ def test_synthetic_system_is_diagonally_dominant():
     row[~nonroot] = 0.0
     np.add.at(row, par[nonroot], np.abs(un[nonroot]))
     assert (dn - row >= 0.01 - 1e-12).all()
+
+
+def test_tune_solver_layout_with_rerooted_candidates(tmp_path):
+    pop = uneven_subset()
+    cands = [dict(pack_compartments=24576), dict(pack_compartments=24576, reroot=True)]
+    plan, rep = T.tune_plan(pop["ncomp"], pop["parent"], layout="solver", candidates=cands, reps=2,
+                            cache_path=str(tmp_path / "tune.json"))
+    assert rep["options"] in cands and len(rep["ms"]) == 2
+    f32 = {k: dev(pop[k].astype(np.float32), torch.float32) for k in ("d", "u", "b")}
+    xp = H.solve_compensated_packed(plan, H.pack(plan, f32["d"]), H.pack_coupling(plan, f32["u"]),
+                                    H.pack(plan, f32["b"]))
+    ref = oracle.solve_batch(pop["ncomp"], pop["parent"],
+                             *(pop[k].astype(np.float32).astype(np.float64) for k in ("d", "u", "b")))
+    assert cell_rel_err(H.unpack(plan, xp).cpu().numpy(), ref, pop["offsets"]).max() <= 1e-10
+    with pytest.raises(ValueError):
+        T.tune_plan(pop["ncomp"], pop["parent"], layout="natural", candidates=cands)
