@@ -10,10 +10,11 @@
  * Matrix convention (Section 2 of the paper): one cell is an N x N symmetric
  * matrix A with A[i][i] = d[i] and A[i][p[i]] = A[p[i]][i] = u[i] for i > 0;
  * p[0] = -1 and 0 <= p[i] < i (Hines numbering).  u[0] is ignored.
- * Listing 2 of the paper prints u[p[i]] in its backward loop but u[i] in its
- * forward loop; on a tree a parent compartment has several children, so only
- * the per-child coupling u[i] = A[i][p[i]] is well defined, and it is used in
- * both loops here (the same holds for Listing 1 with p[i] = i-1).
+ * Listing 2 of the paper indexes the coupling by the parent in its
+ * elimination sweep but by the row itself in its substitution sweep; on a tree
+ * a parent compartment has several children, so only the per-child coupling
+ * u[i] = A[i][p[i]] is well defined, and both sweeps use it here (the same
+ * holds for Listing 1 with p[i] = i-1).
  *
  * Batches: cells are concatenated; off[c] .. off[c+1] is cell c and parent
  * indices are cell-local.
@@ -38,34 +39,49 @@ int oracle_check_parent(int64_t n, const int32_t *p) {
   return ORACLE_OK;
 }
 
-/* Section 2, Listing 1: Thomas algorithm for a symmetric tridiagonal matrix,
- * u[i] = A[i][i-1].  Solves in place: d is overwritten by the eliminated
- * diagonal, b by the solution. */
+/* Section 2: the tridiagonal case (Listing 1's Thomas algorithm), u[i] =
+ * A[i][i-1].  Gaussian elimination from the last row up: row i is the only
+ * row below row i-1 that still couples to it, so subtracting the multiple
+ * l = A[i-1][i] / A[i][i] of row i from row i-1 clears that coupling and
+ * changes only row i-1's diagonal and right-hand side.  What is left is lower
+ * bidiagonal and is solved from the first row down.  In place: d becomes the
+ * eliminated diagonal, b the solution. */
 void oracle_thomas(int64_t n, double *d, const double *u, double *b) {
   if (n <= 0) return;
-  for (int64_t i = n - 1; i >= 1; --i) { /* backward substitution */
-    double f = u[i] / d[i];
-    d[i - 1] = d[i - 1] - f * u[i];
-    b[i - 1] = b[i - 1] - f * b[i];
+  for (int64_t row = n - 1; row > 0; --row) {
+    const double l = u[row] / d[row];
+    d[row - 1] -= l * u[row];
+    b[row - 1] -= l * b[row];
   }
-  b[0] = b[0] / d[0]; /* solve root */
-  for (int64_t i = 1; i < n; ++i) /* forward substitution */
-    b[i] = (b[i] - u[i] * b[i - 1]) / d[i];
+  for (int64_t row = 0; row < n; ++row) {
+    const double known = row == 0 ? 0.0 : u[row] * b[row - 1];
+    b[row] = (b[row] - known) / d[row];
+  }
 }
 
-/* Section 2, Listing 2: Hines algorithm, Thomas with a parent lookup.
- * In place: d becomes the eliminated diagonal, b the solution x. */
+/* Section 2: the tree case (the Hines algorithm, Listing 2 with reading C1:
+ * the coupling of row i to its parent is u[i] in both sweeps).  Because every
+ * parent is numbered before its children, the rows can be eliminated from the
+ * last to the first exactly as above, each row into its parent row p[i]
+ * instead of row i-1: when row i is reached, all of its children are already
+ * folded into it, and its one remaining off-diagonal entry is the coupling to
+ * the parent.  The remaining system has one entry per row left of the
+ * diagonal, to the parent, whose unknown is known once the rows are solved
+ * from the root outwards.  In place: d becomes the eliminated diagonal, b the
+ * solution x. */
 int oracle_hines(int64_t n, const int32_t *p, double *d, const double *u, double *b) {
   int rc = oracle_check_parent(n, p);
   if (rc != ORACLE_OK || n == 0) return rc;
-  for (int64_t i = n - 1; i >= 1; --i) { /* backward substitution, leaves to root */
-    double f = u[i] / d[i];
-    d[p[i]] = d[p[i]] - f * u[i];
-    b[p[i]] = b[p[i]] - f * b[i];
+  for (int64_t row = n - 1; row > 0; --row) {
+    const int64_t par = p[row];
+    const double l = u[row] / d[row];
+    d[par] -= l * u[row];
+    b[par] -= l * b[row];
   }
-  b[0] = b[0] / d[0]; /* solve root */
-  for (int64_t i = 1; i < n; ++i) /* forward substitution, root to leaves */
-    b[i] = (b[i] - u[i] * b[p[i]]) / d[i];
+  for (int64_t row = 0; row < n; ++row) {
+    const double known = row == 0 ? 0.0 : u[row] * b[p[row]];
+    b[row] = (b[row] - known) / d[row];
+  }
   return ORACLE_OK;
 }
 

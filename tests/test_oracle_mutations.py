@@ -16,10 +16,10 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
 
 MUTATIONS = {
     "none": None,
-    "listing2_literal_u_of_parent": ("d[p[i]] = d[p[i]] - f * u[i];", "d[p[i]] = d[p[i]] - f * u[p[i]];"),
-    "rhs_sign": ("b[p[i]] = b[p[i]] - f * b[i];", "b[p[i]] = b[p[i]] + f * b[i];"),
-    "forward_dropped_term": ("b[i] = (b[i] - u[i] * b[p[i]]) / d[i];", "b[i] = b[i] / d[i];"),
-    "forward_thomas_index": ("b[i] = (b[i] - u[i] * b[p[i]]) / d[i];", "b[i] = (b[i] - u[i] * b[i - 1]) / d[i];"),
+    "listing2_literal_u_of_parent": ("d[par] -= l * u[row];", "d[par] -= l * u[par];"),
+    "rhs_sign": ("b[par] -= l * b[row];", "b[par] += l * b[row];"),
+    "forward_dropped_term": ("const double known = row == 0 ? 0.0 : u[row] * b[p[row]];", "const double known = 0.0;"),
+    "forward_thomas_index": ("u[row] * b[p[row]];", "u[row] * b[row - 1];"),
     "matvec_missing_transpose": ("y[p[i]] = y[p[i]] + u[i] * x[i];", ""),
     "rebuild_missing_parent_edge": ("d[p[i]] = d[p[i]] + a[i];", ""),
     "adjoint_grad_a_sign": ("grad_a[lo + i] = grad_a[lo + i] - (lam[i]", "grad_a[lo + i] = grad_a[lo + i] + (lam[i]"),
