@@ -141,13 +141,14 @@ class ClockSampler:
 
 
 def traffic_record(kernel):
-    """ncu DRAM bytes per compartment for `kernel`, if captured on the current sources."""
+    """ncu DRAM bytes per compartment for `kernel`, if captured on the current
+    sources of the task kernels (their code, the planner and the launches)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         from paper_1810_12742_gb300 import _build
         with open(path) as f:
             rec = json.load(f).get(kernel)
-        if rec and rec.get("source_digest") == _build._digest():
+        if rec and rec.get("source_digest") == _build.unit_kernel_digest():
             return float(rec["dram_bytes_per_unknown"])
     except Exception:
         pass

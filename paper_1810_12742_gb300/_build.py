@@ -48,6 +48,24 @@ def _digest(extra=()) -> str:
     return h.hexdigest()
 
 
+# The files that decide what the task kernels k_units<...> do and how the
+# solves launch them: their code, the plan structure they read, the planner
+# that builds the schedule and the entry points that size the grid.  DRAM
+# counters taken on these files stay valid while none of them changes.
+UNIT_KERNEL_FILES = ("csrc/unit_kernels.cu", "csrc/device_common.cuh", "csrc/kernels.h", "csrc/plan.h",
+                     "csrc/plan.cpp", "csrc/hines_abi.cu")
+
+
+def unit_kernel_digest() -> str:
+    h = hashlib.sha256()
+    for rel in UNIT_KERNEL_FILES:
+        h.update(rel.encode())
+        with open(os.path.join(PKG, rel), "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(NVCC_FLAGS + CXX_FLAGS).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link libhines.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
