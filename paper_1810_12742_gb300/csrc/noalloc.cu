@@ -51,10 +51,13 @@ hines_status scratch_for_current_device(double** out) {
   return HINES_OK;
 }
 
-// One thread per cell runs Listing 2 serially; the eliminated diagonal lives
-// in the scratch array at the cell's natural-layout offsets.  A cell whose
-// offsets or parent indices are out of range is left unsolved and its
-// right-hand side is set to NaN, so a bad input never leads to an access
+// One thread per cell solves it serially (Section 2's Hines algorithm, with
+// the per-child coupling u[i] = A[i][p[i]]): rows are folded into their parent
+// rows from the last to the first, which leaves one coupling per row, to the
+// parent, and the rows are then solved from the root outwards.  The eliminated
+// diagonal lives in the scratch array at the cell's natural-layout offsets.  A
+// cell whose offsets or parent indices are out of range is left unsolved and
+// its right-hand side is set to NaN, so a bad input never leads to an access
 // outside the arrays.
 __global__ void k_noalloc_solve(long long n_unknowns, int n_cells, const long long* __restrict__ off,
                                 const int* __restrict__ p, const double* __restrict__ d,
@@ -65,21 +68,27 @@ __global__ void k_noalloc_solve(long long n_unknowns, int n_cells, const long lo
   if (lo < 0 || hi < lo || hi > n_unknowns) return;
   const long long n = hi - lo;
   if (n == 0) return;
-  bool ok = p[lo] == -1;
-  for (long long i = 1; i < n && ok; ++i) ok = p[lo + i] >= 0 && (long long)p[lo + i] < i;
+  const int* pc = p + lo;
+  const double* uc = u + lo;
+  double* bc = b + lo;
+  double* diag = dd + lo;
+  bool ok = pc[0] == -1;
+  for (long long i = 1; i < n && ok; ++i) ok = pc[i] >= 0 && (long long)pc[i] < i;
   if (!ok) {
-    for (long long i = 0; i < n; ++i) b[lo + i] = __longlong_as_double(0x7ff8000000000000LL);
+    for (long long i = 0; i < n; ++i) bc[i] = __longlong_as_double(0x7ff8000000000000LL);
     return;
   }
-  for (long long i = 0; i < n; ++i) dd[lo + i] = d[lo + i];
-  for (long long i = n - 1; i >= 1; --i) {
-    const long long q = lo + p[lo + i];
-    const double f = u[lo + i] / dd[lo + i];
-    dd[q] -= f * u[lo + i];
-    b[q] -= f * b[lo + i];
+  for (long long i = 0; i < n; ++i) diag[i] = d[lo + i];
+  for (long long row = n - 1; row > 0; --row) {  // fold row into its parent row
+    const int par = pc[row];
+    const double l = uc[row] / diag[row];
+    diag[par] -= l * uc[row];
+    bc[par] -= l * bc[row];
   }
-  b[lo] = b[lo] / dd[lo];
-  for (long long i = 1; i < n; ++i) b[lo + i] = (b[lo + i] - u[lo + i] * b[lo + p[lo + i]]) / dd[lo + i];
+  for (long long row = 0; row < n; ++row) {  // root outwards: the parent's unknown is known
+    const double known = row == 0 ? 0.0 : uc[row] * bc[pc[row]];
+    bc[row] = (bc[row] - known) / diag[row];
+  }
 }
 
 }  // namespace

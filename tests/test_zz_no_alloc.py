@@ -1,9 +1,9 @@
 """Allocation-free solve entry point (hines_solve_f64_noalloc), for callers
 that may not allocate device memory and therefore cannot create a plan.
 
-Called through the C-ABI with ctypes and checked against the plan-based
-FP64 solve (hines_solve) within the FP64 parity tolerance, on two calls in a
-row (the second call finds the first call's values in the shared scratch
+Called through the C-ABI with ctypes and checked against the oracle and the
+plan-based FP64 solve (hines_solve) within the FP64 parity tolerance, on two
+calls in a row (the second call finds the first call's values in the shared scratch
 array).  This file is collected last so that a failure here stops a -x run
 only after every other test has run."""
 import ctypes
@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1810_12742_gb300 import hines as H
 from tests.helpers import problem, tree_zoo
 
@@ -47,6 +48,7 @@ def test_noalloc_matches_plan_solve_twice():
     H.solve(plan, d, u, ref)
     off = dev(plan.offsets, torch.int64)
     par = dev(parent, torch.int32)
+    exact = oracle.solve_batch(ncomp, parent, c["d"], c["u"], c["b"])
     for rep in range(2):
         x = dev(c["b"] * (1.0 + rep))
         assert _noalloc(n, len(ncomp), off, par, d, u, x) == H.HINES_OK
@@ -56,6 +58,8 @@ def test_noalloc_matches_plan_solve_twice():
         for k in range(len(ncomp)):
             sl = slice(plan.offsets[k], plan.offsets[k + 1])
             assert np.abs(got[sl] - want[sl]).max() <= 1e-12 * np.abs(want[sl]).max()
+            scale = np.abs(exact[sl]).max() * (1.0 + rep)
+            assert np.abs(got[sl] - exact[sl] * (1.0 + rep)).max() <= 1e-12 * scale
 
 
 def test_noalloc_rejects_oversized_batch():
