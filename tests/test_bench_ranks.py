@@ -42,3 +42,19 @@ def test_single_rank_needs_no_process_group():
     assert not dist.is_initialized()
     assert bench.reduce_max(3.5, 1, "cpu") == 3.5
     assert bench.job_value(10, 4, 1, 2.0) == pytest.approx(20000.0)
+
+
+def test_traffic_record_follows_the_kernel_sources(monkeypatch):
+    """roofline.traffic is reported only while the task kernels' sources are
+    the ones the DRAM counters were taken on."""
+    import json
+    import os
+
+    from paper_1810_12742_gb300 import _build
+    rec = json.load(open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")))
+    key = "k_units<CompMode>"
+    monkeypatch.setattr(_build, "unit_kernel_digest", lambda: rec[key]["source_digest"])
+    assert bench.traffic_record(key) == rec[key]["dram_bytes_per_unknown"]
+    monkeypatch.setattr(_build, "unit_kernel_digest", lambda: "0" * 64)
+    assert bench.traffic_record(key) is None
+    assert bench.traffic_record("no such kernel") is None
