@@ -374,8 +374,10 @@ def test_tasks_respect_lane_rule_and_cover_branches():
         assert sel.sum() > 0
 
 
-def test_planner_time_is_linear():
-    """Section 6: the setup work is linear in the number of cells."""
+@pytest.mark.parametrize("reroot", [False, True])
+def test_planner_time_is_linear(reroot):
+    """Section 6: the setup work, balancing included, is linear in the number
+    of cells."""
     import time
     w = I.WORKLOADS["fp64_uniform"]
     ncomp, parent = I.population_trees(w, np.arange(64))
@@ -385,7 +387,7 @@ def test_planner_time_is_linear():
         pa = np.tile(parent, rep)
         t0 = time.perf_counter()
         for _ in range(3):
-            H.Plan(nc, pa, split_branches=True, host_only=True)
+            H.Plan(nc, pa, split_branches=True, host_only=True, reroot=reroot)
         t.append((time.perf_counter() - t0) / 3)
     assert t[1] < 8 * t[0] * 2.5  # linear within noise
 
