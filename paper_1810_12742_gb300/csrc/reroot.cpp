@@ -18,7 +18,11 @@
 #include "reroot.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
+#include <exception>
+#include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/hines.h"
@@ -151,19 +155,44 @@ int reroot_batch(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, R
   out.perm.resize((size_t)n);
   out.edge.resize((size_t)n);
   out.centre.resize((size_t)n_cells);
-  std::vector<int32_t> perm, edge;
-  for (int64_t off = 0, c = 0; c < n_cells; off += ncomp[c], ++c) {
-    const int32_t m = ncomp[c];
-    perm.resize((size_t)m);
-    edge.resize((size_t)m);
-    const int32_t root = m > 0 ? tree_centre(m, parent + off) : 0;
-    out.centre[(size_t)c] = root;
-    reroot_cell(m, parent + off, root, out.parent.data() + off, perm.data(), edge.data());
-    for (int32_t j = 0; j < m; ++j) {
-      out.perm[(size_t)(off + j)] = off + perm[(size_t)j];
-      out.edge[(size_t)(off + j)] = edge[(size_t)j] >= 0 ? off + edge[(size_t)j] : -1;
+  std::vector<int64_t> off((size_t)n_cells + 1, 0);
+  for (int32_t c = 0; c < n_cells; ++c) off[(size_t)c + 1] = off[(size_t)c] + ncomp[c];
+  // cells are independent: worker threads take cells in turn and write
+  // disjoint ranges of the outputs
+  std::atomic<int32_t> next_cell{0};
+  std::atomic<bool> oom{false};
+  auto work = [&]() {
+    try {
+      std::vector<int32_t> perm, edge;
+      for (int32_t c = next_cell++; c < n_cells && !oom; c = next_cell++) {
+        const int64_t o = off[(size_t)c];
+        const int32_t m = ncomp[c];
+        perm.resize((size_t)m);
+        edge.resize((size_t)m);
+        const int32_t root = m > 0 ? tree_centre(m, parent + o) : 0;
+        out.centre[(size_t)c] = root;
+        reroot_cell(m, parent + o, root, out.parent.data() + o, perm.data(), edge.data());
+        for (int32_t j = 0; j < m; ++j) {
+          out.perm[(size_t)(o + j)] = o + perm[(size_t)j];
+          out.edge[(size_t)(o + j)] = edge[(size_t)j] >= 0 ? o + edge[(size_t)j] : -1;
+        }
+      }
+    } catch (const std::bad_alloc&) {
+      oom = true;
     }
+  };
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int64_t by_size = n / 65536 + 1;  // no thread for less than about 64K compartments
+  const int n_threads = (int)std::min<int64_t>({(int64_t)(hw > 0 ? hw : 1), 32, by_size, (int64_t)n_cells});
+  std::vector<std::thread> pool;
+  try {  // fewer workers if threads cannot be had; this thread works too
+    pool.reserve((size_t)n_threads);
+    for (int t = 1; t < n_threads; ++t) pool.emplace_back(work);
+  } catch (const std::exception&) {
   }
+  work();
+  for (auto& th : pool) th.join();
+  if (oom) return HINES_ERR_OOM;
   return HINES_OK;
 }
 
