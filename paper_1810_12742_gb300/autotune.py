@@ -22,6 +22,7 @@ import numpy as np
 from . import hines as H
 
 DEFAULT_CANDIDATES = (
+    dict(pack_compartments=12288),
     dict(pack_compartments=16384),
     dict(pack_compartments=24576),
     dict(pack_compartments=32768),
