@@ -202,11 +202,18 @@ def test_solve_compensated_zoo_edge_cases():
         assert cell_rel_err(x.cpu().numpy(), ref, plan.offsets).max() <= TOL_REFINE
 
 
-@pytest.mark.parametrize("margin,tol", [(1e-1, TOL_REFINE), (1e-3, TOL_REFINE), (1e-5, 1e-9)])
-def test_solve_compensated_margin_sweep(margin, tol):
-    """Leak margins of the mixed-precision workload: error grows with the
-    conditioning; at margin 1e-5 (Skeel condition ~5e5) the FP64 oracle itself
-    carries ~cond * 1e-16 error, so the bound there is 1e-9."""
+@pytest.mark.parametrize("margin", [
+    1e-1,
+    1e-3,
+    pytest.param(1e-5, marks=pytest.mark.xfail(
+        strict=True, reason="at margin 1e-5 (Skeel condition ~9e5) the compensated solve reaches about 3.3e-10 "
+                            "against the oracle: above the 1e-10 gate; the refined path must be used there")),
+])
+def test_solve_compensated_margin_sweep(margin):
+    """Leak margins of the mixed-precision workload, every cell held to the
+    FP32-input gate 1e-10.  Double-float arithmetic carries about 48 bits, so
+    the error grows like cond * 2^-48; at margin 1e-5 the compensated solve
+    misses the gate (an expected, strict failure)."""
     w = I.WORKLOADS["uneven_mixed"]
     cls = I.cell_classes(w)
     cells = np.concatenate([np.nonzero(cls == 0)[0][:24], np.nonzero(cls == 1)[0][:3]])
@@ -215,7 +222,7 @@ def test_solve_compensated_margin_sweep(margin, tol):
     plan = H.Plan(pop["ncomp"], pop["parent"])
     x = H.solve_compensated(plan, *(dev(f[k], torch.float32) for k in ("d", "u", "b")))
     ref = oracle.solve_batch(pop["ncomp"], pop["parent"], *(f[k].astype(np.float64) for k in ("d", "u", "b")))
-    assert cell_rel_err(x.cpu().numpy(), ref, plan.offsets).max() <= tol
+    assert cell_rel_err(x.cpu().numpy(), ref, plan.offsets).max() <= TOL_REFINE
 
 
 def test_solve_compensated_deterministic():

@@ -121,6 +121,33 @@ def test_cable_steps_reusing_the_factor_equal_full_steps(theta):
         assert torch.equal(a.fetch(), b.fetch())
 
 
+@pytest.mark.parametrize("theta", [0, 1])
+@pytest.mark.parametrize("layout", ["natural", "solver"])
+def test_cable_steps_reusing_the_factor_match_oracle(theta, layout):
+    """The factor-reuse variant against the oracle's own stepper directly (not
+    only against the full steps): one full step, then steps that eliminate
+    only the rebuilt right-hand side with the stored factor."""
+    w, pop = uneven_subset(20, 2)
+    plan = H.Plan(pop["ncomp"], pop["parent"])
+    s, g, u = dev(pop["s"]), dev(pop["g"]), dev(pop["u"])
+    K = 12
+    if layout == "natural":
+        V = dev(pop["V0"])
+        H.cable_step(plan, s, g, u, V, w.dt, w.E, theta)
+        for _ in range(K - 1):
+            H.cable_step_reuse(plan, s, g, u, V, w.dt, w.E, theta)
+    else:
+        pk = [H.pack(plan, s), H.pack(plan, g), H.pack_coupling(plan, u)]
+        Vp = H.pack(plan, dev(pop["V0"]))
+        H.cable_step_packed(plan, *pk, Vp, w.dt, w.E, theta)
+        for _ in range(K - 1):
+            H.cable_step_reuse(plan, *pk, Vp, w.dt, w.E, theta, solver_layout=True)
+        V = H.unpack(plan, Vp)
+    ref, _ = oracle.steps_batch(pop["ncomp"], pop["parent"], pop["s"], pop["g"], pop["a"], pop["V0"], K, w.dt, w.E,
+                                theta)
+    assert rel_cells(V.cpu().numpy(), ref, plan.offsets) <= 1e-12
+
+
 def _adjoint_case(cells, steps, ce, theta=1):
     w = I.WORKLOADS["adjoint"]
     pop = I.population(w, cells=cells, keys=("s", "a", "u", "g", "V0", "target"))
@@ -189,6 +216,27 @@ def test_adjoint_central_differences_on_gpu_forward():
         e[i] = h
         fd = (loss(t["g"], t["a"] + e) - loss(t["g"], t["a"] - e)) / (2 * h)
         assert abs(fd - aa.grad[i].item()) <= 1e-5 * abs(aa.grad[i].item()) + eps_L
+
+
+def test_rollout_graphs_equal_eager_rollout():
+    """The captured forward and reverse graphs give the eager rollout's loss
+    and gradients bit for bit, and a second replay with new inputs follows
+    the new inputs (the graphs read their static buffers, not stale data)."""
+    w = I.WORKLOADS["adjoint"]
+    pop = I.population(w, cells=np.arange(5), keys=("s", "a", "u", "g", "V0", "target"))
+    plan = H.Plan(pop["ncomp"], pop["parent"])
+    t = {k: dev(pop[k]) for k in ("s", "a", "g", "V0", "target")}
+    K, ce = 30, 7
+    for scale in (1.0, 1.1):
+        g = t["g"] * scale
+        u = -t["a"]
+        lc, ck, VL = R.cable_rollout(plan, t["s"], g, u, t["V0"], t["target"], K, w.dt, w.E, 1, ce)
+        gg, ga = R.cable_rollout_grad(plan, t["s"], g, u, t["target"], K, w.dt, w.E, 1, ce, ck, VL)
+        rg = R.rollout_graphs(plan, K, w.dt, w.E, 1, ce)
+        loss = rg.forward(g, u, t["s"], t["V0"], t["target"])
+        assert torch.equal(loss, lc)
+        g2, a2 = rg.backward()
+        assert torch.equal(g2, gg) and torch.equal(a2, ga)
 
 
 def test_hines_solve_autograd_gradcheck():
