@@ -371,22 +371,27 @@ hines_status hines_cable_loss_seed(hines_plan_t plan, const double *V, const dou
  * memory (a host runtime whose device allocator is fixed at start-up, a
  * memory pool that forbids new allocations, code that must not change the
  * process's device footprint).  Such callers cannot create a plan, because
- * plan creation allocates; this call needs none.  It solves every cell of the
- * batch in place with one GPU thread per cell, and keeps the eliminated
- * diagonal in a fixed device array inside the library (16 MiB per GPU that
- * loads the library, held until the process exits).  No paper counterpart:
- * it is the serial algorithm of Listing 2 with its scratch preallocated.
+ * plan creation allocates; this call needs none.  The paper has no
+ * counterpart: it is a plain serial tree solve run by one GPU thread per
+ * cell (each unbranched run eliminated as a chain, folded into its parent
+ * row where a branch starts, then substituted from the root outwards), with
+ * its scratch -- the eliminated diagonal and one validity word -- kept in a
+ * fixed device array inside the library (16 MiB per GPU that loads the
+ * library, held until the process exits).
  *   n_unknowns    total compartments, 0 .. 2,097,152 (larger: HINES_ERR_INVALID_ARG)
- *   n_cells       >= 0
- *   cell_offsets  device int64[n_cells + 1], natural-layout offsets
+ *   n_cells       >= 0 (0: nothing to do, HINES_OK)
+ *   cell_offsets  device int64[n_cells + 1], natural-layout offsets: off[0] = 0,
+ *                 non-decreasing, off[n_cells] <= n_unknowns
  *   parent        device int32[n_unknowns], cell-local parent arrays
  *   d, u          device double[n_unknowns], not modified
  *   b_inout       device double[n_unknowns]: right-hand side in, solution out
- * Stream-ordered.  A cell whose offsets or parent array are invalid is left
- * with NaN in b_inout.  The first call on a device looks up the device
- * address of the scratch array, so make it before any stream capture.  All
- * calls share the scratch array: calls whose work may overlap on the GPU
- * (unordered streams) race on it.
+ * Stream-ordered.  The checks of the device arrays run on the GPU, so they
+ * cannot be returned: offsets that break the rule above leave every entry of
+ * b_inout NaN and solve nothing; a cell whose parent array breaks Hines order
+ * is left NaN while the other cells are solved.  The first call on a device
+ * looks up the device address of the scratch array, so make it before any
+ * stream capture.  All calls share the scratch array: calls whose work may
+ * overlap on the GPU (unordered streams) race on it.
  */
 hines_status hines_solve_f64_noalloc(int64_t n_unknowns, int32_t n_cells, const int64_t *cell_offsets,
                                      const int32_t *parent, const double *d, const double *u, double *b_inout,

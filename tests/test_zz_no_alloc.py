@@ -62,6 +62,55 @@ def test_noalloc_matches_plan_solve_twice():
             assert np.abs(got[sl] - exact[sl] * (1.0 + rep)).max() <= 1e-12 * scale
 
 
+def test_noalloc_bad_parent_cell_is_nan_others_solved():
+    """A cell whose parent array breaks Hines order comes back NaN; the cells
+    around it are still solved and match the oracle."""
+    ncomp, parent, c = _batch(42)
+    bad = int(np.nonzero(ncomp > 5)[0][1])  # a cell of the zoo with more than five compartments
+    off = np.concatenate(([0], np.cumsum(ncomp))).astype(np.int64)
+    par = parent.copy()
+    par[off[bad] + 2] = 5  # p[i] >= i breaks Hines order
+    n = int(ncomp.sum())
+    dev = lambda a, t=torch.float64: torch.as_tensor(np.ascontiguousarray(a)).to("cuda", t)  # noqa: E731
+    x = dev(c["b"])
+    assert _noalloc(n, len(ncomp), dev(off, torch.int64), dev(par, torch.int32), dev(c["d"]), dev(c["u"]),
+                    x) == H.HINES_OK
+    got = x.cpu().numpy()
+    exact = oracle.solve_batch(ncomp, parent, c["d"], c["u"], c["b"])
+    for k in range(len(ncomp)):
+        sl = slice(off[k], off[k + 1])
+        if k == bad:
+            assert np.isnan(got[sl]).all()
+        else:
+            assert np.abs(got[sl] - exact[sl]).max() <= 1e-12 * np.abs(exact[sl]).max()
+
+
+def test_noalloc_bad_offsets_leave_nan_and_empty_batch_is_ok():
+    ncomp, parent, c = _batch(43)
+    n = int(ncomp.sum())
+    dev = lambda a, t=torch.float64: torch.as_tensor(np.ascontiguousarray(a)).to("cuda", t)  # noqa: E731
+    off = np.concatenate(([0], np.cumsum(ncomp))).astype(np.int64)
+    off[2], off[3] = off[3], off[2]  # not non-decreasing: two cells would overlap
+    x = dev(c["b"])
+    assert _noalloc(n, len(ncomp), dev(off, torch.int64), dev(parent, torch.int32), dev(c["d"]), dev(c["u"]),
+                    x) == H.HINES_OK
+    assert torch.isnan(x).all()
+    # no cells: nothing to do, nothing touched
+    y = dev(c["b"])
+    assert H.lib().hines_solve_f64_noalloc(n, 0, None, None, None, None, None, None) == H.HINES_OK
+    assert torch.equal(y, dev(c["b"]))
+    # a valid call afterwards still solves (the validity word is rewritten by every call)
+    good = np.concatenate(([0], np.cumsum(ncomp))).astype(np.int64)
+    x = dev(c["b"])
+    assert _noalloc(n, len(ncomp), dev(good, torch.int64), dev(parent, torch.int32), dev(c["d"]), dev(c["u"]),
+                    x) == H.HINES_OK
+    exact = oracle.solve_batch(ncomp, parent, c["d"], c["u"], c["b"])
+    got = x.cpu().numpy()
+    for k in range(len(ncomp)):
+        sl = slice(good[k], good[k + 1])
+        assert np.abs(got[sl] - exact[sl]).max() <= 1e-12 * np.abs(exact[sl]).max()
+
+
 def test_noalloc_rejects_oversized_batch():
     big = (1 << 21) + 1
     assert H.lib().hines_solve_f64_noalloc(big, 1, None, None, None, None, None, None) == H.HINES_ERR_INVALID_ARG
