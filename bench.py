@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (64-cell, 16384-cell, margin sweep, adjoint)")
-    ap.add_argument("--cable-steps", type=int, default=100,
+    ap.add_argument("--cable-steps", type=int, default=1000,
                     help="passive-cable steps per captured graph for the time-stepping figure (0: skip)")
     ap.add_argument("--only", choices=["headline", "solver_layout"],
                     help="run only this solve, warmup + steps times, and print its time (small profiling runs)")
@@ -285,7 +285,7 @@ def other_configs(torch, H, oracle, stream, max_over_ranks):
 
     # branching-probability sweep (the Fig. 7.2 experiment, on 16384-cell-shaped
     # cells): the warp-task FP64 solve against the one-thread-per-cell serial
-    # solve (hines_solve_f64_noalloc, Listing 2 per thread), same data
+    # solve (hines_solve_f64_noalloc: one serial tree solve per thread), same data
     import ctypes
     import dataclasses
     base = I.WORKLOADS["fp64_uniform"]
@@ -324,17 +324,29 @@ def other_configs(torch, H, oracle, stream, max_over_ranks):
     pop = I.population(w, keys=("s", "a", "u", "g", "V0", "target"))
     plan = H.Plan(pop["ncomp"], pop["parent"])
     tt = {k: torch.as_tensor(pop[k]).cuda() for k in ("s", "a", "g", "V0", "target")}
-    ga = tt["g"].clone().requires_grad_(True)
-    aa = tt["a"].clone().requires_grad_(True)
-    torch.cuda.synchronize()
+
+    def rollout_once():
+        ga_ = tt["g"].clone().requires_grad_(True)
+        aa_ = tt["a"].clone().requires_grad_(True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        L_ = R.CableRollout.apply(ga_, aa_, plan, tt["s"], tt["V0"], tt["target"], w.steps, w.dt, w.E, 1,
+                                  w.checkpoint_every)
+        ev[1].record(stream)
+        L_.backward()
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        return L_, ga_, aa_, ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+
     t0 = time.perf_counter()
-    L = R.CableRollout.apply(ga, aa, plan, tt["s"], tt["V0"], tt["target"], w.steps, w.dt, w.E, 1,
-                             w.checkpoint_every)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    L.backward()
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
+    rollout_once()  # builds and captures the forward and reverse graphs
+    build_s = time.perf_counter() - t0
+    rollout_once()
+    runs = [rollout_once() for _ in range(5)]
+    L, ga, aa = runs[-1][:3]
+    fwd_ms = max_over_ranks(float(np.median([r[3] for r in runs])))
+    bwd_ms = max_over_ranks(float(np.median([r[4] for r in runs])))
     loss, rg, ra = oracle.adjoint_batch(pop["ncomp"], pop["parent"], pop["s"], pop["g"], pop["a"], pop["V0"],
                                         pop["target"], w.steps, w.dt, w.E, 1, nthreads=nth)
     gg, gaa = ga.grad.cpu().numpy(), aa.grad.cpu().numpy()
@@ -342,7 +354,10 @@ def other_configs(torch, H, oracle, stream, max_over_ranks):
     mask = np.ones(gaa.size, bool)
     mask[roots] = False
     out["adjoint"] = {"steps": w.steps, "compartments": int(pop["offsets"][-1]),
-                      "forward_ms": (t1 - t0) * 1e3, "backward_ms": (t2 - t1) * 1e3,
+                      "forward_ms": fwd_ms, "backward_ms": bwd_ms, "repeats": len(runs),
+                      "timing": "median of 5 after 2 warm-up rollouts (CUDA events); the first rollout builds "
+                                "and captures the forward and reverse graphs",
+                      "graph_build_s": build_s,
                       "loss_rel_err": abs(L.item() - float(loss.sum())) / abs(float(loss.sum())),
                       "grad_g_rel_err": float(np.abs(gg - rg).max() / np.abs(rg).max()),
                       "grad_a_rel_err": float(np.abs(gaa[mask] - ra[mask]).max() / np.abs(ra[mask]).max())}
@@ -629,8 +644,10 @@ def main():
                         "roofline_frac": BYTES_F32_IN * n / (ms_ref * 1e-3) / 1e9 / peak},
         "e2e": {"value": n_job / (e2e_ms * 1e-3), "unit": "compartments/s",
                 "h2d_bytes_per_step": 12 * n_job, "d2h_bytes_per_step": 8 * n_job, "max_rel_err": e2e_err,
-                "path": f"HostPipeline.solve_compensated: pinned host arrays, {args.e2e_pieces} pieces, "
-                        "transfers overlapped with the solves"},
+                "path": f"Python hines.HostPipeline.solve_compensated: pinned host arrays, cut into "
+                        f"{args.e2e_pieces} pieces of consecutive cells; torch copies on three streams overlap "
+                        "each piece's host-to-device copy, its C-ABI device solve (hines_solve_compensated) and "
+                        "its device-to-host copy"},
         "clocks": clk.summary(),
         "gpu_launches": 2 * args.steps,
     }

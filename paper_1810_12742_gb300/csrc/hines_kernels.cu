@@ -73,7 +73,8 @@ __global__ void k_cable_loss_accumulate(DevPlan P, const double* __restrict__ V,
 int grid_for_branches(const DevPlan& P) {
   const int64_t warps = P.n_branches;
   const int64_t blocks = (warps * 32 + 255) / 256;
-  return (int)(blocks < 152 * 16 ? (blocks > 0 ? blocks : 1) : 152 * 16);
+  const int64_t cap = (int64_t)P.sms * 16;  // 16 blocks of 256 threads per multiprocessor at most
+  return (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
 }
 
 }  // namespace

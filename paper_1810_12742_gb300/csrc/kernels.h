@@ -52,6 +52,7 @@ struct DevPlan {
   const int64_t* pk_perm = nullptr;       // [n_packed] natural index of each solver-layout slot, -1 for padding
   const int64_t* pk_edge = nullptr;       // [n_packed] natural index of each slot's coupling (pk_perm unless re-rooted)
   int32_t grid[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // persistent grid size per kernel kind
+  int32_t sms = 1;                             // multiprocessors of the plan's device
   // workspace
   void* fac = nullptr;    // 8 bytes per natural or solver-layout slot: factor (FP64 / FP32 solves), FP32 working
                           // arrays (refine)

@@ -154,9 +154,10 @@ __global__ void k_relres(DevPlan P, const double* __restrict__ bstat, double* __
   }
 }
 
-int grid_for(int64_t items, int per_block) {
-  const int64_t b = (items + per_block - 1) / per_block;
-  return (int)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
+// enough blocks to cover the items, at most 32 per multiprocessor of the plan's device
+int grid_for(const DevPlan& P, int64_t items, int per_block) {
+  const int64_t b = (items + per_block - 1) / per_block, cap = (int64_t)P.sms * 32;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 }  // namespace
@@ -174,9 +175,9 @@ cudaError_t launch_unit_refine(const DevPlan& P, const float* d, const float* u,
   double* prev = static_cast<double*>(P.red);          // [n_cells] largest correction of the last step
   double* bcorr = static_cast<double*>(P.cb);          // [nb] largest correction per branch
   double* bstat = bcorr + P.n_branches;                // [nb][3] residual maxima per branch
-  const int blocks_b = grid_for((P.n_branches + 1) / 2 * 32, 256);
-  const int blocks_n = grid_for(n, 256);
-  const int blocks_c = grid_for((int64_t)nc * 32, 256);
+  const int blocks_b = grid_for(P, (P.n_branches + 1) / 2 * 32, 256);
+  const int blocks_n = grid_for(P, n, 256);
+  const int blocks_c = grid_for(P, (int64_t)nc * 32, 256);
   e = cudaMemcpyAsync(xf, b, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = launch_unit_solve_f32(P, d, u, xf, s);
   if (e == cudaSuccess) {

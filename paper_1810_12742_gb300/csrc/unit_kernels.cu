@@ -750,7 +750,12 @@ using PkCableReuse = FactorMode<double, true, true, true>;
 }  // namespace
 
 cudaError_t prepare_unit_kernels(DevPlan& P) {
-  cudaError_t e = grid_of<F64>(P, &P.grid[0]);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  P.sms = sms > 0 ? sms : 1;
+  e = grid_of<F64>(P, &P.grid[0]);
   if (e == cudaSuccess) e = grid_of<F32>(P, &P.grid[1]);
   if (e == cudaSuccess) e = grid_of<Cable>(P, &P.grid[2]);
   if (e == cudaSuccess) e = grid_of<CompMode>(P, &P.grid[3]);

@@ -190,7 +190,7 @@ WORKLOADS = {
                              16384, (_C1,), (1.0,)),
     "uneven_steps": Workload("uneven_steps: 8192 cells (70% small, 30% large), passive cable, 1000 steps", 2, 2,
                              8192, (_C2S, _C2L), (0.7, 0.3), steps=1000),
-    "uneven_mixed": Workload("uneven_mixed: uneven population, FP32 storage + refinement", 3, 2,
+    "uneven_mixed": Workload("uneven_mixed: 8192 cells (70% small, 30% large), FP32 d, u, b in, FP64 x out", 3, 2,
                              8192, (_C2S, _C2L), (0.7, 0.3)),
     "adjoint": Workload("adjoint: 256 cells x U[100,500] branches x 16 compartments, 200 steps", 4, 4,
                         256, (_C4,), (1.0,), steps=200, checkpoint_every=20),

@@ -11,7 +11,12 @@ calls, captures them in a CUDA graph and keeps the checkpoints.
   with the states checkpointed every ``checkpoint_every`` steps and each
   segment recomputed during the reverse sweep.  The matrix is symmetric, so
   the adjoint of a step is one more Hines solve (hines_cable_solve).
-* ``HinesSolve`` and ``CableRollout``: torch.autograd.Function wrappers.
+* ``RolloutGraphs``: the same forward rollout and reverse sweep, each
+  captured once in a CUDA graph over static buffers and replayed (a rollout
+  of a small batch is hundreds of short launches; the graph removes their
+  launch cost).
+* ``HinesSolve`` and ``CableRollout``: torch.autograd.Function wrappers
+  (``CableRollout`` replays the graphs of ``RolloutGraphs``).
 """
 from __future__ import annotations
 
@@ -111,23 +116,114 @@ def cable_rollout_grad(plan: H.Plan, s, g, u, target, steps: int, dt: float, E: 
     return grad_g, grad_a
 
 
+class RolloutGraphs:
+    """The forward rollout and the checkpointed reverse sweep of
+    ``cable_rollout`` / ``cable_rollout_grad``, each captured once in a CUDA
+    graph over static buffers.  ``forward(g, u, s, V0, target)`` copies the
+    inputs in and replays the forward graph (loss per cell, checkpoints and
+    the last state stay in the object's buffers); ``backward()`` replays the
+    reverse sweep on them and returns (dL/dg, dL/da) buffers.  The same
+    kernels run in the same order as the eager functions, so the results are
+    bit-identical to them."""
+
+    def __init__(self, plan: H.Plan, steps: int, dt: float, E: float, theta: int, checkpoint_every: int):
+        self.plan, self.cfg = plan, (steps, dt, E, theta, checkpoint_every)
+        n, nc = plan.n_unknowns, plan.n_cells
+        f = dict(dtype=torch.float64, device="cuda")
+        self.g, self.u, self.s, self.V0 = (torch.zeros(n, **f) for _ in range(4))
+        self.target = torch.zeros(nc, **f)
+        self.loss = torch.zeros(nc, **f)
+        nseg = (steps + checkpoint_every - 1) // checkpoint_every
+        self.ckpt = [torch.zeros(n, **f) for _ in range(nseg)]
+        self.V = torch.zeros(n, **f)
+        self.states = [torch.zeros(n, **f) for _ in range(checkpoint_every + 1)]
+        self.grad_g, self.grad_a, self.vbar, self.lam = (torch.zeros(n, **f) for _ in range(4))
+        # the first step creates nothing lazily, but run each body once eagerly
+        # so that every kernel has been loaded before capture
+        self._fwd_body()
+        self._bwd_body()
+        torch.cuda.synchronize()
+        self.fwd_graph, self.bwd_graph = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.fwd_graph):
+            self._fwd_body()
+        with torch.cuda.graph(self.bwd_graph):
+            self._bwd_body()
+
+    def _fwd_body(self):
+        plan = self.plan
+        steps, dt, E, theta, ce = self.cfg
+        n = plan.n_unknowns
+        self.loss.zero_()
+        self.V.copy_(self.V0)
+        self.ckpt[0].copy_(self.V0)
+        for k in range(1, steps + 1):
+            H.cable_step(plan, self.s, self.g, self.u, self.V, dt, E, theta)
+            H.lib().hines_cable_loss_accumulate(plan.handle, H._dptr(self.V, torch.float64, n, "V"),
+                                                H._dptr(self.target, torch.float64, plan.n_cells, "target"),
+                                                H._dptr(self.loss, torch.float64, plan.n_cells, "loss"), H._stream())
+            if k % ce == 0 and k < steps:
+                self.ckpt[k // ce].copy_(self.V)
+
+    def _bwd_body(self):
+        plan = self.plan
+        steps, dt, E, theta, ce = self.cfg
+        s, g, u, target = self.s, self.g, self.u, self.target
+        self.grad_g.zero_()
+        self.grad_a.zero_()
+        self.vbar.zero_()
+        H.cable_loss_seed(plan, self.V, target, self.vbar)
+        for seg in range(len(self.ckpt) - 1, -1, -1):
+            k0 = seg * ce
+            k1 = min(steps, k0 + ce)
+            self.states[0].copy_(self.ckpt[seg])
+            for j in range(k1 - k0):
+                self.states[j + 1].copy_(self.states[j])
+                H.cable_step(plan, s, g, u, self.states[j + 1], dt, E, theta)
+            for k in range(k1, k0, -1):
+                self.lam.copy_(self.vbar)
+                H.cable_solve(plan, s, g, u, self.lam, dt, theta)
+                H.cable_adjoint_step(plan, self.lam, self.states[k - k0], self.states[k - 1 - k0], s, g, target, dt,
+                                     E, theta, int(k - 1 >= 1), self.grad_g, self.grad_a, self.vbar)
+
+    def forward(self, g, u, s, V0, target):
+        for dst, src in ((self.g, g), (self.u, u), (self.s, s), (self.V0, V0), (self.target, target)):
+            dst.copy_(src)
+        self.fwd_graph.replay()
+        return self.loss
+
+    def backward(self):
+        self.bwd_graph.replay()
+        return self.grad_g, self.grad_a
+
+
+def rollout_graphs(plan: H.Plan, steps: int, dt: float, E: float, theta: int, checkpoint_every: int):
+    """The plan's RolloutGraphs for this configuration (built on first use,
+    then kept on the plan object)."""
+    cache = plan.__dict__.setdefault("_rollout_graphs", {})
+    key = (int(steps), float(dt), float(E), int(theta), int(checkpoint_every))
+    if key not in cache:
+        cache[key] = RolloutGraphs(plan, *key)
+    return cache[key]
+
+
 class CableRollout(torch.autograd.Function):
-    """loss = CableRollout.apply(g, a, plan, s, V0, target, steps, dt, E, theta, checkpoint_every)"""
+    """loss = CableRollout.apply(g, a, plan, s, V0, target, steps, dt, E, theta, checkpoint_every)
+
+    Forward and backward replay the plan's captured rollout graphs
+    (``rollout_graphs``); the returned gradients are copies of the graphs'
+    buffers.  Two rollouts on the same plan and configuration share those
+    buffers, so one's backward must run before the other's forward."""
 
     @staticmethod
     def forward(ctx, g, a, plan, s, V0, target, steps, dt, E, theta=1, checkpoint_every=20):
-        u = torch.neg(a)
-        loss, ckpt, V_last = cable_rollout(plan, s, g, u, V0, target, steps, dt, E, theta, checkpoint_every)
-        ctx.plan, ctx.cfg = plan, (steps, dt, E, theta, checkpoint_every)
-        ctx.ckpt, ctx.V_last = ckpt, V_last
-        ctx.save_for_backward(g, u, s, target)
+        rg = rollout_graphs(plan, steps, dt, E, theta, checkpoint_every)
+        loss = rg.forward(g.detach(), torch.neg(a.detach()), s, V0, target)
+        ctx.rg = rg
         return loss.sum()
 
     @staticmethod
     def backward(ctx, gL):
-        g, u, s, target = ctx.saved_tensors
-        steps, dt, E, theta, ce = ctx.cfg
-        grad_g, grad_a = cable_rollout_grad(ctx.plan, s, g, u, target, steps, dt, E, theta, ce, ctx.ckpt, ctx.V_last)
+        grad_g, grad_a = ctx.rg.backward()
         return gL * grad_g, gL * grad_a, None, None, None, None, None, None, None, None, None
 
 
