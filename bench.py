@@ -62,6 +62,8 @@ def parse():
                     help="skip the other workloads (64-cell, 16384-cell, margin sweep, adjoint)")
     ap.add_argument("--cable-steps", type=int, default=1000,
                     help="passive-cable steps per captured graph for the time-stepping figure (0: skip)")
+    ap.add_argument("--per-lane", type=int, default=0, choices=[0, 1, 2],
+                    help="branch pieces per warp lane of the plan (0: the library's default)")
     ap.add_argument("--only", choices=["headline", "solver_layout"],
                     help="run only this solve, warmup + steps times, and print its time (small profiling runs)")
     return ap.parse_args()
@@ -438,7 +440,7 @@ def main():
         return reduce_max(v, world, "cuda")
 
     t_plan = time.perf_counter()
-    plan = H.Plan(pop["ncomp"], pop["parent"])
+    plan = H.Plan(pop["ncomp"], pop["parent"], pieces_per_lane=args.per_lane)
     config["plan_create_s"] = time.perf_counter() - t_plan  # host planner + upload, once per morphology
     f32 = {k: torch.as_tensor(pop[k].astype(np.float32)).cuda() for k in ("d", "u", "b")}
     x = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -536,11 +538,15 @@ def main():
     err64 = max_rel_err(x64, False)
     del f64, x64
 
-    # FP32 elimination + FP64 residual refinement (the same FP32 inputs)
+    # FP32 elimination + residual refinement (the same FP32 inputs): the FP32
+    # solve, then per step one pass that forms the residual and eliminates it
+    # with the FP32 factor, and one that substitutes the correction
     xr = torch.empty(n, dtype=torch.float64, device="cuda")
-    ms_ref = timed(lambda: H.solve_refine(plan, f32["d"], f32["u"], f32["b"], xr, args.refine_steps),
-                   args.refine_reps)
-    err_ref = max_rel_err(xr, True)
+    refine = {}
+    for st in sorted({1, args.refine_steps}):
+        ms_r = timed(lambda: H.solve_refine(plan, f32["d"], f32["u"], f32["b"], xr, st), args.refine_reps)
+        refine[st] = (ms_r, max_rel_err(xr, True))
+    ms_ref, err_ref = refine[args.refine_steps]
     del xr
 
     # the same solve on arrays kept in the solver layout (Section 5's per-chunk
@@ -641,7 +647,13 @@ def main():
         "configs": configs,
         "fp32_refine": {"value": n / (ms_ref * 1e-3), "unit": "compartments/s", "ms_per_solve": ms_ref,
                         "refine_steps": args.refine_steps, "max_rel_err": err_ref,
-                        "roofline_frac": BYTES_F32_IN * n / (ms_ref * 1e-3) / 1e9 / peak},
+                        "roofline_frac": BYTES_F32_IN * n / (ms_ref * 1e-3) / 1e9 / peak,
+                        "speedup_over_fp64": ms64 / ms_ref,
+                        "steps": {str(k): {"ms_per_solve": v[0], "max_rel_err": v[1],
+                                           "roofline_frac": BYTES_F32_IN * n / (v[0] * 1e-3) / 1e9 / peak}
+                                  for k, v in refine.items()},
+                        "path": "hines_solve_refine: FP32 solve (factor kept), then per step a residual + "
+                                "correction-elimination pass and a correction-substitution pass"},
         "e2e": {"value": n_job / (e2e_ms * 1e-3), "unit": "compartments/s",
                 "h2d_bytes_per_step": 12 * n_job, "d2h_bytes_per_step": 8 * n_job, "max_rel_err": e2e_err,
                 "path": f"Python hines.HostPipeline.solve_compensated: pinned host arrays, cut into "

@@ -65,9 +65,14 @@ enum { HINES_F64 = 0, HINES_F32 = 1 };
 typedef struct {
   int32_t host_only;       /* 1: build the host-side plan only (no CUDA calls); it can be
                               inspected with hines_plan_info / hines_plan_export but not solved */
-  int32_t split_branches;  /* 1: split branches longer than their level's mean (Section 6) */
-  int32_t cta_threads;     /* 0, or a multiple of 32 in 32..1024 (validated; no kernel of this
-                              version takes a CTA size from it) */
+  int32_t split_branches;  /* 1: split branches longer than their level's mean over the batch
+                              (Section 6); 2: longer than their level's mean within their own
+                              cell (a local variant, the per-block averages of the paper's
+                              outlook after Section 7); 0: no split */
+  int32_t pieces_per_lane; /* branch pieces a warp lane owns in a chunk: 0 or 1 (default) for
+                              one (chunks of up to 32 pieces), 2 for two (chunks of up to 64;
+                              the lane runs both chains at once, the compensated solve with
+                              packed FP32-pair instructions); other values HINES_ERR_INVALID_ARG */
   int32_t sort_by_length;  /* 1: among ready branches equally far from their unit root, take the
                               longer first (Section 4, Fig. 4.1); 0: by cell and branch index,
                               so that a chunk of a breadth-first numbered cell reads contiguous runs */
@@ -113,12 +118,15 @@ typedef struct {
  * 16 compartments into near-equal chained pieces, assigns levels (number of
  * ancestor branches), cuts cells of more than 4096 compartments into a top
  * part and subtrees, packs these units into warp tasks (by size, or by
- * Section 4's greedy rule with the 32 lanes of a warp), cuts every task into
- * chunks of at most 32 branches by Hu's list schedule (a branch joins a chunk
- * once its children in the task are in earlier chunks, deepest first), lays
- * out the solver layout (Section 5), and uploads the metadata and a workspace
- * to the current device.  On success *out receives the plan; on failure *out
- * is NULL.
+ * Section 4's greedy rule with the lanes of a warp), cuts every task into
+ * chunks of at most 32 * pieces_per_lane branches by Hu's list schedule (a
+ * branch joins a chunk once its children in the task are in earlier chunks,
+ * deepest first; within a chunk, longest first), lays out the solver layout
+ * (Section 5), and uploads the metadata and a workspace to the current
+ * device.  Branches longer than 16 are cut from their proximal end into
+ * pieces that each reach the farthest multiple of 8 (in the natural layout)
+ * within 16 compartments, or the branch's end.  On success *out receives the
+ * plan; on failure *out is NULL.
  */
 hines_status hines_plan_create(hines_plan_t *out, int32_t n_cells, const int32_t *ncomp, const int32_t *parent,
                                const hines_plan_opts *opts);
@@ -169,12 +177,16 @@ hines_status hines_plan_export_tasks(hines_plan_t plan, int64_t *branch_task, in
 /*
  * The solver layout (Section 5: the data of the branches a warp solves
  * together, interleaved so that each step reads one contiguous run).  Every
- * chunk -- at most 32 branches of one level of a warp task, one per lane --
- * owns a block starting on a multiple of 4 slots; row r of the block holds
- * the r-th compartment counted from the distal end of every branch of the
- * chunk longer than r, in lane order.  A solver-layout array has
- * info.n_packed elements (n_unknowns plus padding slots) and must be
- * 16-byte aligned.
+ * chunk of a warp task owns a block starting on a multiple of 4 slots.  With
+ * one piece per lane, row r of the block holds the r-th compartment counted
+ * from the distal end of every branch of the chunk longer than r, in chunk
+ * order.  With two pieces per lane the chunk's branches pair up (2j, 2j + 1,
+ * the first the longer), the two aligned at their proximal ends: row r holds
+ * two slots for every pair whose longer branch is longer than r -- that
+ * branch's r-th compartment from its distal end, and the compartment of the
+ * shorter one at the same distance from the proximal end, or a padding slot.
+ * A solver-layout array has info.n_packed elements (n_unknowns plus padding
+ * slots) and must be 16-byte aligned.
  *
  * hines_plan_export_packed: host int64[n_packed], the natural-layout index
  * held by each slot, -1 for a padding slot (for a re-rooted plan: the index in

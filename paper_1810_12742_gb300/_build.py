@@ -52,7 +52,8 @@ def _digest(extra=()) -> str:
 # solves launch them: their code, the plan structure they read, the planner
 # that builds the schedule and the entry points that size the grid.  DRAM
 # counters taken on these files stay valid while none of them changes.
-UNIT_KERNEL_FILES = ("csrc/unit_kernels.cu", "csrc/device_common.cuh", "csrc/kernels.h", "csrc/plan.h",
+UNIT_KERNEL_FILES = ("csrc/unit_kernels.cuh", "csrc/unit_kernels_p1.cu", "csrc/unit_kernels_p2.cu",
+                     "csrc/unit_dispatch.cu", "csrc/device_common.cuh", "csrc/kernels.h", "csrc/plan.h",
                      "csrc/plan.cpp", "csrc/hines_abi.cu")
 
 

@@ -111,6 +111,130 @@ __device__ __forceinline__ ff ff_mul(ff f, ff b) {
   return {Q, q};
 }
 
+// ---- one or two independent values per thread -------------------------------
+// The solve kernels give a lane one or two branch pieces.  Their arithmetic is
+// written once over a value type V: float for one piece, F2 for two, whose
+// operations are the packed FP32 pair instructions of sm_100 and later (one
+// instruction performs the operation on both halves, each rounded to nearest
+// like its FP32 counterpart; no fusing or contraction happens across them).
+struct F2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ F2 f2_make(float a, float b) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float f2_lo(F2 a) { return __uint_as_float((unsigned)a.v); }
+__device__ __forceinline__ float f2_hi(F2 a) { return __uint_as_float((unsigned)(a.v >> 32)); }
+__device__ __forceinline__ F2 vadd(F2 a, F2 b) {
+  F2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 vsub(F2 a, F2 b) {
+  F2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 vmul(F2 a, F2 b) {
+  F2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) {
+  F2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ F2 vneg(F2 a) { return vmul(a, f2_make(-1.f, -1.f)); }
+__device__ __forceinline__ F2 vrcp(F2 a) { return f2_make(rcp_t(f2_lo(a)), rcp_t(f2_hi(a))); }
+__device__ __forceinline__ F2 vsplat(float a, F2) { return f2_make(a, a); }
+
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float vrcp(float a) { return rcp_t(a); }
+__device__ __forceinline__ float vsplat(float a, float) { return a; }
+
+// Double-float over V: the same error-free transformations as ff above.
+template <typename V>
+struct FFV {
+  V h, l;
+};
+// fast two-sum, |h| >= |l|
+template <typename V>
+__device__ __forceinline__ FFV<V> vrenorm(V h, V l) {
+  const V s = vadd(h, l);
+  return {s, vsub(l, vsub(s, h))};
+}
+// (x, 0) - (yh + yl) with a full two-sum on the leading parts
+template <typename V>
+__device__ __forceinline__ FFV<V> vsub_ff(V x, V yh, V yl) {
+  const V s = vsub(x, yh);
+  const V bb = vsub(s, x);
+  const V e = vsub(vsub(x, vsub(s, bb)), vadd(yh, bb));
+  return vrenorm(s, vsub(e, yl));
+}
+// (x, 0) - (yh + yl) when |x| >= |yh| (the diagonal chain of a diagonally
+// dominant matrix: d_{i-1} > u_i^2 / d'_i), fast two-sum on the leading parts
+template <typename V>
+__device__ __forceinline__ FFV<V> vsub_dom(V x, V yh, V yl) {
+  const V s = vsub(x, yh);
+  const V e = vsub(vsub(x, s), yh);
+  return vrenorm(s, vsub(e, yl));
+}
+// (x.h + x.l) - (yh + yl), full two-sum on the leading parts
+template <typename V>
+__device__ __forceinline__ FFV<V> vsub_ffff(FFV<V> x, V yh, V yl) {
+  const V s = vsub(x.h, yh);
+  const V bb = vsub(s, x.h);
+  const V e = vsub(vsub(x.h, vsub(s, bb)), vadd(yh, bb));
+  return vrenorm(s, vadd(e, vsub(x.l, yl)));
+}
+// u / D for a plain u: r = 1/D.h, F = u r, t = u - F D (exact leading part by
+// FMA), quotient F + t r, renormalised.  nF = -F carries the sign so that
+// both FMAs take their operands as they are.
+template <typename V>
+__device__ __forceinline__ FFV<V> vdiv_f(V u, FFV<V> D) {
+  const V r = vrcp(D.h);
+  const V F = vmul(u, r);
+  const V nF = vneg(F);
+  V t = vfma(nF, D.h, u);
+  t = vfma(nF, D.l, t);
+  return vrenorm(F, vmul(t, r));
+}
+// N / D
+template <typename V>
+__device__ __forceinline__ FFV<V> vdiv(FFV<V> N, FFV<V> D) {
+  const V r = vrcp(D.h);
+  const V X = vmul(N.h, r);
+  const V nX = vneg(X);
+  V t = vfma(nX, D.h, N.h);
+  t = vadd(t, N.l);
+  t = vfma(nX, D.l, t);
+  return vrenorm(X, vmul(t, r));
+}
+// f * u for a plain u: the leading product, its exact error by FMA, plus f.l u
+template <typename V>
+__device__ __forceinline__ FFV<V> vmul_f(FFV<V> f, V u) {
+  const V P = vmul(f.h, u);
+  V p = vfma(f.h, u, vneg(P));
+  p = vfma(f.l, u, p);
+  return {P, p};
+}
+// f * b
+template <typename V>
+__device__ __forceinline__ FFV<V> vmul_ff(FFV<V> f, FFV<V> b) {
+  const V Q = vmul(f.h, b.h);
+  V q = vfma(f.h, b.h, vneg(Q));
+  q = vfma(f.h, b.l, q);
+  q = vfma(f.l, b.h, q);
+  return {Q, q};
+}
+
 // hi + lo rounded to FP64 with integer operations on the bit pattern (no FP64
 // pipe): hi is widened exactly by re-biasing its exponent, lo is scaled to
 // units of the last place of that double and added to the bit pattern.  Rare

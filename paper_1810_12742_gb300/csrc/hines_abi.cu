@@ -81,6 +81,7 @@ hines_status upload(hines_plan_t p) {
       {H.cell_top_task.data(), H.cell_top_task.size() * 4, (const void**)&D.cell_top_task},
       {H.counter_init.data(), H.counter_init.size() * 4, (const void**)&D.counter_init},
       {H.task_sub.data(), H.task_sub.size() * 4, (const void**)&D.task_sub},
+      {H.torder.data(), H.torder.size() * 4, (const void**)&D.pos_branch},
       {H.cell_off.data(), H.cell_off.size() * 8, (const void**)&D.cell_off},
       {H.br_first.data(), H.br_first.size() * 8, (const void**)&D.br_first},
       {H.br_len.data(), H.br_len.size() * 4, (const void**)&D.br_len},
@@ -114,8 +115,8 @@ hines_status upload(hines_plan_t p) {
   const size_t fac_b = align256(std::max(n, (size_t)H.n_packed) * 8 + 8), cd_b = align256(nb * 16 + 16),
                cb_b = align256(nb * 32 + 32),
                ds_b = align256(nb * 16 + 16), xl_b = align256(nb * 8 + 8), red_b = align256(nc * 8 + 8),
-               cnt_b = align256((nc + 4) * 4);
-  const size_t wtotal = fac_b + cd_b + cb_b + ds_b + xl_b + red_b + cnt_b;
+               cnt_b = align256((nc + 4) * 4), rw_b = align256(std::max(n, (size_t)H.n_packed) * 4 + 4);
+  const size_t wtotal = fac_b + cd_b + cb_b + ds_b + xl_b + red_b + cnt_b + rw_b;
   if (cudaMalloc(&p->work, wtotal) != cudaSuccess) {
     cudaGetLastError();
     p->work = nullptr;
@@ -137,7 +138,10 @@ hines_status upload(hines_plan_t p) {
   w += red_b;
   D.counter = reinterpret_cast<int32_t*>(w);
   D.cell_pending = D.counter + 4;
+  w += cnt_b;
+  D.rw = w;
   D.n_wtasks = H.n_tasks;
+  D.per_lane = H.per_lane;
   D.n_packed = H.n_packed;
   for (int k = 0; k < 4; ++k) D.phase_off[k] = H.phase_off.empty() ? 0 : H.phase_off[(size_t)k];
   D.n_cells = H.n_cells;
@@ -181,8 +185,8 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
   for (int k = 0; k < 2; ++k)
     if (o.reserved[k] != 0) return HINES_ERR_INVALID_ARG;
   if (o.pack_compartments < -1) return HINES_ERR_INVALID_ARG;
-  if (o.cta_threads == 0) o.cta_threads = 256;
-  if (o.cta_threads < 32 || o.cta_threads > 1024 || (o.cta_threads % 32) != 0) return HINES_ERR_INVALID_ARG;
+  if (o.pieces_per_lane == 0) o.pieces_per_lane = 1;
+  if (o.pieces_per_lane != 1 && o.pieces_per_lane != 2) return HINES_ERR_INVALID_ARG;
   hines_plan_t p = new (std::nothrow) hines_plan_s();
   if (!p) return HINES_ERR_OOM;
   int rc;
@@ -191,7 +195,7 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
     rc = p->rerooted ? hines::reroot_batch(n_cells, ncomp, parent, p->rr) : HINES_OK;
     if (rc == HINES_OK)
       rc = hines::build_host_plan(n_cells, ncomp, p->rerooted ? p->rr.parent.data() : parent, o.split_branches,
-                                  o.sort_by_length, o.pack_compartments, p->host);
+                                  o.sort_by_length, o.pack_compartments, o.pieces_per_lane, p->host);
     if (rc == HINES_OK && p->rerooted) {
       // the solver layout maps straight to the caller's numbering: node arrays
       // through the renumbering, couplings through the edge map

@@ -45,6 +45,7 @@ struct DevPlan {
   const int32_t* counter_init = nullptr;  // [4 + n_cells] values restored before every solve
   const int32_t* cell_top_task = nullptr; // [n_cells] task of the cell's top part, -1 if not cut
   const int32_t* task_sub = nullptr;      // [2 * n_wtasks] (cell, subtree units) of a subtree task
+  const int32_t* pos_branch = nullptr;    // [nb] branch id (natural numbering) of each position
   int32_t* cell_pending = nullptr;        // counter + 4: subtree units whose elimination is still to finish
   // solver layout (Section 5's interleaving per chunk)
   int64_t n_packed = 0;
@@ -53,6 +54,8 @@ struct DevPlan {
   const int64_t* pk_edge = nullptr;       // [n_packed] natural index of each slot's coupling (pk_perm unless re-rooted)
   int32_t grid[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // persistent grid size per kernel kind
   int32_t sms = 1;                             // multiprocessors of the plan's device
+  int32_t per_lane = 2;                        // branch pieces per warp lane (the plan's lane mapping)
+  int32_t grid_refine = 1;                     // persistent grid size of the refinement steps
   // workspace
   void* fac = nullptr;    // 8 bytes per natural or solver-layout slot: factor (FP64 / FP32 solves), FP32 working
                           // arrays (refine)
@@ -61,11 +64,35 @@ struct DevPlan {
   void* dstate = nullptr; // n_branches * 16 bytes: folded distal state per position (compensated)
   void* xlast = nullptr;  // n_branches * 8 bytes: solution at the distal compartment per position
   void* red = nullptr;    // n_cells * 8 bytes: per-cell reductions
+  void* rw = nullptr;     // 4 bytes per natural or solver-layout slot: the refinement's eliminated residual
   int32_t* status = nullptr;  // device status word
 };
 
-// Warp-task kernels (unit_kernels.cu).  prepare_unit_kernels sets their
-// shared-memory limits and persistent grid sizes once per plan.
+// One call of the warp-task kernels (unit_kernels.cuh): the mode and its arrays.
+enum class UnitOp {
+  F64, F32, F32Resolve, Comp, Cable, CableReuse, PkF64, PkF32, PkComp, PkCable, PkCableReuse,
+  // refinement steps on the FP32 factor (natural layout): x in FP32 or as a
+  // double-float pair, x + c out as a pair or in FP64
+  Refine32to2, Refine32to64, Refine2to2, Refine2to64
+};
+struct UnitCall {
+  UnitOp op = UnitOp::F64;
+  const void* d = nullptr;
+  const void* u = nullptr;
+  const void* b = nullptr;
+  void* x = nullptr;  // right-hand side in / solution out (compensated: the FP64 solution)
+  const void* s = nullptr;
+  const void* g = nullptr;
+  double dt = 0.0, E = 0.0;
+  int theta = 1;
+  bool rhs_from_V = true;
+  const void* rhs = nullptr;  // FP32 factor solve: right-hand side read instead of x (x then receives the solution)
+  float* rw = nullptr;        // refinement: eliminated residual per compartment
+  float* bcorr = nullptr;     // refinement: per branch the largest |correction| of the step
+};
+
+// Warp-task kernels (unit_kernels.cuh, unit_dispatch.cu).  prepare_unit_kernels
+// sets their shared-memory limits and persistent grid sizes once per plan.
 cudaError_t prepare_unit_kernels(DevPlan& P);
 cudaError_t launch_unit_solve_f64(const DevPlan& P, const double* d, const double* u, double* b, cudaStream_t s);
 cudaError_t launch_unit_solve_f32(const DevPlan& P, const float* d, const float* u, float* b, cudaStream_t s);
@@ -91,7 +118,15 @@ cudaError_t launch_pack(const DevPlan& P, int elem_bytes, const void* natural, v
                         bool coupling = false);
 cudaError_t launch_unpack(const DevPlan& P, int elem_bytes, const void* packed, void* natural, cudaStream_t s);
 
-// FP32 elimination + FP64 residual refinement on the warp-task kernels (refine_kernels.cu).
+// FP32 solve of rhs into x (x receives the solution; rhs is not modified).
+cudaError_t launch_unit_solve_f32_rhs(const DevPlan& P, const float* d, const float* u, const float* rhs, float* x,
+                                      cudaStream_t s);
+// One refinement step on the FP32 factor (natural layout): x (FP32, or double-float pairs when x_pairs) in,
+// x + c out (double-float pairs, or FP64 when final); per branch the largest |c| into bcorr.
+cudaError_t launch_unit_refine_step(const DevPlan& P, const float* d, const float* u, const float* b, const void* x,
+                                    bool x_pairs, void* xo, bool final, float* bcorr, cudaStream_t s);
+
+// FP32 elimination + residual refinement on the warp-task kernels (refine_kernels.cu).
 cudaError_t launch_unit_refine(const DevPlan& P, const float* d, const float* u, const float* b, double* x, int steps,
                                double* relres, cudaStream_t s);
 

@@ -53,11 +53,14 @@ void decompose(int64_t n, const int32_t* p, std::vector<int32_t>& nchild, std::v
   }
 }
 
-// One level of Section 6's splitting over the whole batch: every branch on
-// `level` longer than the level's mean length (mean in FP64, strict >) is cut
-// after ceil(len/2) compartments; the distal piece becomes a child branch one
-// level deeper and takes over the children.  Returns true if the level exists.
-bool split_level(std::vector<std::vector<Br>>& cells, int32_t level) {
+// One level of Section 6's splitting: every branch on `level` longer than
+// the level's mean length (mean in FP64, strict >) is cut after ceil(len/2)
+// compartments; the distal piece becomes a child branch one level deeper and
+// takes over the children.  The mean is taken over the whole batch (global),
+// or, with `local`, over each cell's own branches on the level (the local
+// heuristic of the paper's outlook: averages per block of work instead of
+// over all trees).  Returns true if some cell has the level.
+bool split_level(std::vector<std::vector<Br>>& cells, int32_t level, bool local) {
   double sum = 0.0;
   int64_t cnt = 0;
   for (auto& bs : cells)
@@ -67,10 +70,22 @@ bool split_level(std::vector<std::vector<Br>>& cells, int32_t level) {
         cnt++;
       }
   if (cnt == 0) return false;
-  const double mean = sum / (double)cnt;
+  const double global_mean = sum / (double)cnt;
   std::vector<Br> nb;
   std::vector<int32_t> remap_prox, remap_dist;
   for (auto& bs : cells) {
+    double mean = global_mean;
+    if (local) {
+      double csum = 0.0;
+      int64_t ccnt = 0;
+      for (auto& b : bs)
+        if (b.level == level) {
+          csum += (double)b.len;
+          ccnt++;
+        }
+      if (ccnt == 0) continue;
+      mean = csum / (double)ccnt;
+    }
     bool any = false;
     for (auto& b : bs)
       if (b.level == level && (double)b.len > mean && b.len >= 2) any = true;
@@ -108,10 +123,15 @@ bool split_level(std::vector<std::vector<Br>>& cells, int32_t level) {
   return true;
 }
 
-// Cut every branch longer than `cap` into ceil(len / cap) chained pieces of
-// near-equal length (the first len % pieces pieces, counted from the proximal
-// end, are one longer).  The system is unchanged; only the schedule is.
-void cap_branches(std::vector<Br>& bs, int32_t cap) {
+// Cut every branch longer than `cap` into chained pieces of at most `cap`
+// compartments whose boundaries fall on multiples of kCutAlign natural
+// indices (`base` is the cell's offset in the natural layout): from the
+// proximal end, each piece reaches the farthest such boundary within `cap`
+// compartments, or the branch's end.  A piece then never shares a 32-byte
+// sector of an FP32 array with the next piece of its branch, so the chunks
+// that load them (at different times) do not fetch a sector twice.  The
+// system is unchanged; only the schedule is.
+void cap_branches(std::vector<Br>& bs, int32_t cap, int64_t base) {
   bool any = false;
   for (auto& b : bs) any |= b.len > cap;
   if (!any) return;
@@ -119,18 +139,23 @@ void cap_branches(std::vector<Br>& bs, int32_t cap) {
   std::vector<int32_t> last_piece(bs.size());
   for (size_t j = 0; j < bs.size(); ++j) {
     const Br b = bs[j];
-    const int32_t pieces = (b.len + cap - 1) / cap, base = b.len / pieces, rem = b.len % pieces;
-    int64_t first = b.first;
     int32_t parent = b.parent < 0 ? -1 : last_piece[(size_t)b.parent];
-    for (int32_t k = 0; k < pieces; ++k) {
+    const int64_t end = b.first + b.len;
+    int64_t start = b.first;
+    while (start < end) {
+      int64_t stop = std::min<int64_t>(end, start + cap);
+      if (stop < end) {
+        const int64_t down = stop - (base + stop) % kCutAlign;  // aligned boundary at or below stop
+        if (down > start) stop = down;
+      }
       Br q;
-      q.first = first;
-      q.len = base + (k < rem ? 1 : 0);
+      q.first = start;
+      q.len = (int32_t)(stop - start);
       q.parent = parent;
       q.level = parent < 0 ? 0 : nb[(size_t)parent].level + 1;
       parent = (int32_t)nb.size();
-      first += q.len;
       nb.push_back(q);
+      start = stop;
     }
     last_piece[j] = parent;
   }
@@ -140,10 +165,13 @@ void cap_branches(std::vector<Br>& bs, int32_t cap) {
 }  // namespace
 
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,
-                    int sort_by_length, int pack_compartments, HostPlan& P) {
+                    int sort_by_length, int pack_compartments, int pieces_per_lane, HostPlan& P) {
   if (n_cells < 0 || (n_cells > 0 && !ncomp)) return HINES_ERR_INVALID_ARG;
+  if (pieces_per_lane != 1 && pieces_per_lane != 2) return HINES_ERR_INVALID_ARG;
   P = HostPlan();
   P.n_cells = n_cells;
+  P.per_lane = pieces_per_lane;
+  const int32_t width = kLanes * pieces_per_lane;  // pieces per chunk
   P.cell_off.assign((size_t)n_cells + 1, 0);
   for (int32_t c = 0; c < n_cells; ++c) {
     if (ncomp[c] < 0) return HINES_ERR_INVALID_ARG;
@@ -166,10 +194,11 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
     }
     decompose(n, p, nchild, branch_of, cells[(size_t)c]);
   }
+  if (split_branches < 0 || split_branches > 2) return HINES_ERR_INVALID_ARG;
   if (split_branches)
-    for (int32_t level = 0; split_level(cells, level); ++level) {
+    for (int32_t level = 0; split_level(cells, level, split_branches == 2); ++level) {
     }
-  for (auto& bs : cells) cap_branches(bs, kBranchCap);
+  for (int32_t c = 0; c < n_cells; ++c) cap_branches(cells[(size_t)c], kBranchCap, P.cell_off[(size_t)c]);
 
   // flatten to global branch ids (cell by cell, by first compartment)
   P.cell_br_off.assign((size_t)n_cells + 1, 0);
@@ -346,7 +375,7 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
       if (fits && kind == 1 && units[(size_t)groups.back()[0]].cell != units[(size_t)u].cell) fits = false;
       if (fits && lane_rule) {
         for (size_t l = 0; l < ucnt.size(); ++l)
-          if ((l < cnt.size() ? cnt[l] : 0) + ucnt[l] > kLanes) {
+          if ((l < cnt.size() ? cnt[l] : 0) + ucnt[l] > width) {
             fits = false;
             break;
           }
@@ -377,10 +406,13 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
       }
       // chunks by Hu's list schedule for in-forests: a branch is ready once
       // all its children in the task sit in earlier chunks; each chunk takes
-      // the (at most 32) ready branches farthest from their unit's root,
-      // ties by length (with sort_by_length), cell, branch.  This needs the
-      // fewest chunks for the task's dependency forest; levels of the kernel
-      // are these chunks, stored root-side first.
+      // the (at most 32 per lane) ready branches farthest from their unit's
+      // root, ties by length (with sort_by_length), cell, branch.  This needs
+      // the fewest chunks for the task's dependency forest; levels of the
+      // kernel are these chunks, stored root-side first.  Within a chunk the
+      // branches are then ordered by length, longest first (stable), so that
+      // the lanes' pieces shrink together and the rows of the solver layout
+      // are prefixes of the chunk.
       for (int32_t b : ids) P.br_task[(size_t)b] = t;
       auto later = [&](int32_t x, int32_t y) {  // priority-queue order: true if x goes after y
         if (P.br_rlevel[(size_t)x] != P.br_rlevel[(size_t)y]) return P.br_rlevel[(size_t)x] < P.br_rlevel[(size_t)y];
@@ -401,10 +433,12 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
       std::vector<int32_t> done;
       while (!ready.empty()) {
         chunks.emplace_back();
-        while (!ready.empty() && (int)chunks.back().size() < kLanes) {
+        while (!ready.empty() && (int)chunks.back().size() < width) {
           chunks.back().push_back(ready.top());
           ready.pop();
         }
+        std::stable_sort(chunks.back().begin(), chunks.back().end(),
+                         [&](int32_t x, int32_t y) { return P.br_len[(size_t)x] > P.br_len[(size_t)y]; });
         for (int32_t b : chunks.back()) {
           const int32_t pb = P.br_parent[(size_t)b];
           if (pb >= 0 && P.br_task[(size_t)pb] == t && --pend[(size_t)pb] == 0) done.push_back(pb);
@@ -482,54 +516,54 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
     int32_t w = P.tchild_ptr[k];
     for (int32_t c = P.child_ptr[(size_t)b]; c < P.child_ptr[(size_t)b + 1]; ++c) P.tchild[(size_t)w++] = P.tpos[(size_t)P.child[(size_t)c]];
   }
-  // solver layout: blocks in task order, levels ascending, chunks of 32
+  // solver layout: blocks in task order, levels ascending, chunks of the
+  // chunk width; row layout as described in plan.h
   {
-    std::vector<int32_t> chunk_c0((size_t)nb, 0);
+    const int32_t per = pieces_per_lane;
     P.pk_blk.assign((size_t)nb, 0);
+    P.pk_pcomp.assign((size_t)nb, -1);
+    std::vector<int64_t> distal((size_t)nb, -1);  // solver-layout index of each position's distal compartment
+    std::vector<int64_t> slots;
     int64_t off = 0;
     for (int32_t t = 0; t < P.n_tasks; ++t) {
       const int32_t* lp = P.tlvl_ptr.data() + P.task_lvl_off[(size_t)t];
       for (int32_t l = 0; l < P.task_nlvl[(size_t)t]; ++l) {
-        for (int32_t c0 = lp[l]; c0 < lp[l + 1]; c0 += kLanes) {
-          const int32_t c1 = std::min(c0 + kLanes, lp[l + 1]);
+        for (int32_t c0 = lp[l]; c0 < lp[l + 1]; c0 += width) {
+          const int32_t c1 = std::min(c0 + width, lp[l + 1]);
+          const int32_t n = c1 - c0, lanes = (n + per - 1) / per;
+          auto len_at = [&](int32_t i) { return i < n ? P.br_len[(size_t)P.torder[(size_t)(c0 + i)]] : 0; };
           int64_t e = 0;
-          for (int32_t q = c0; q < c1; ++q) {
-            e += P.br_len[(size_t)P.torder[(size_t)q]];
-            P.pk_blk[(size_t)q] = off;
-            chunk_c0[(size_t)q] = c0;
+          for (int32_t r = 0; r < kBranchCap; ++r) {
+            for (int32_t j = 0; j < lanes; ++j) {
+              const int32_t rows = len_at(per * j);  // the lane's rows: its longer (first) piece
+              if (rows <= r) continue;
+              for (int32_t h = 0; h < per; ++h) {
+                const int32_t i = per * j + h, len = len_at(i);
+                // distance from the proximal end of the piece at row r (pieces
+                // of a pair are aligned at their proximal ends)
+                const int32_t t_prox = rows - 1 - r;
+                int64_t nat = -1;
+                if (i < n && t_prox < len) {
+                  nat = P.br_first[(size_t)P.torder[(size_t)(c0 + i)]] + t_prox;
+                  if (t_prox == len - 1) distal[(size_t)(c0 + i)] = off + e;
+                }
+                slots.push_back(nat);
+                ++e;
+              }
+            }
           }
-          off += (e + kPackAlign - 1) / kPackAlign * kPackAlign;
+          for (int32_t q = c0; q < c1; ++q) P.pk_blk[(size_t)q] = off;
+          const int64_t padded = (e + kPackAlign - 1) / kPackAlign * kPackAlign;
+          for (int64_t k = e; k < padded; ++k) slots.push_back(-1);
+          off += padded;
         }
       }
     }
     P.n_packed = off;
-    P.pk_perm.assign((size_t)off, -1);
-    P.pk_pcomp.assign((size_t)nb, -1);
+    P.pk_perm.swap(slots);
     for (int32_t q = 0; q < (int32_t)nb; ++q) {
       const int32_t pb = P.br_parent[(size_t)P.torder[(size_t)q]];
-      if (pb >= 0) {
-        const int32_t pq = P.tpos[(size_t)pb];
-        P.pk_pcomp[(size_t)q] = P.pk_blk[(size_t)pq] + (pq - chunk_c0[(size_t)pq]);  // row 0, every lane present
-      }
-    }
-    for (int32_t q = 0; q < (int32_t)nb;) {
-      const int32_t c0 = q;
-      int32_t c1 = q;
-      while (c1 < (int32_t)nb && chunk_c0[(size_t)c1] == c0) ++c1;
-      int64_t row_off = 0;
-      for (int32_t r = 0; r < kBranchCap; ++r) {
-        int64_t rank = 0;
-        for (int32_t j = c0; j < c1; ++j) {
-          const int32_t b = P.torder[(size_t)j];
-          const int32_t len = P.br_len[(size_t)b];
-          if (len > r) {
-            P.pk_perm[(size_t)(P.pk_blk[(size_t)c0] + row_off + rank)] = P.br_first[(size_t)b] + (len - 1 - r);
-            ++rank;
-          }
-        }
-        row_off += rank;
-      }
-      q = c1;
+      if (pb >= 0) P.pk_pcomp[(size_t)q] = distal[(size_t)P.tpos[(size_t)pb]];
     }
   }
   return HINES_OK;

@@ -55,20 +55,33 @@ struct HostPlan {
   std::vector<int32_t> counter_init;   // [4 + n_cells] work counters (0) then cell_nsub
   std::vector<int32_t> task_sub;       // [2 * n_tasks] (cell, subtree units) of a subtree task, else (-1, 0)
 
-  // Solver layout (Section 5's interleaving, per chunk): each chunk -- at
-  // most 32 consecutive positions of one task level -- owns a block; row r of
-  // the block holds the r-th compartment from the distal end of every branch
-  // of the chunk longer than r, in lane order, so a warp reads a row as one
-  // contiguous run.  Blocks start on multiples of kPackAlign compartments.
+  // Pieces per lane: a chunk holds at most 32 * per_lane pieces; lane j of a
+  // warp owns the chunk's pieces per_lane * j .. per_lane * j + per_lane - 1.
+  // Within a chunk the pieces are sorted by length, longest first.
+  int32_t per_lane = 1;
+
+  // Solver layout (Section 5's interleaving, per chunk): each chunk owns a
+  // block.  One piece per lane: row r of the block holds the r-th compartment
+  // from the distal end of every piece of the chunk longer than r, in chunk
+  // order.  Two pieces per lane: the pieces pair up as the lanes own them
+  // (2j, 2j + 1; the first is the longer); a pair spans as many rows as its
+  // longer piece has compartments, the two pieces aligned at their proximal
+  // ends, and row r holds two slots for every pair longer than r: the longer
+  // piece's r-th compartment from its distal end, and the shorter piece's
+  // compartment at the same distance from the proximal end (a padding slot
+  // where the shorter piece has none).  So a warp reads a row as one
+  // contiguous run, each lane its two values as one 8-byte word.  Blocks start
+  // on multiples of kPackAlign compartments.
   int64_t n_packed = 0;
   std::vector<int64_t> pk_blk;    // [nb] block offset of the chunk of each position
   std::vector<int64_t> pk_pcomp;  // [nb] solver-layout index of the parent branch's distal compartment, -1 at a root
   std::vector<int64_t> pk_perm;   // [n_packed] natural index held by each solver-layout slot, -1 for padding
 };
 
-constexpr int kLanes = 32;       // branches per chunk (one per lane)
+constexpr int kLanes = 32;       // lanes of a warp; a chunk holds 32 * per_lane pieces
 constexpr int kBranchCap = 16;   // maximum compartments per branch after capping
-constexpr int kWarpsPerCta = 4;  // warps per CTA of the task kernels (each warp runs its own task)
+constexpr int kWarpsPerCta = 2;  // warps per CTA of the task kernels (each warp runs its own task)
+constexpr int64_t kCutAlign = 8; // pieces of a cut branch start on multiples of 8 natural indices (32-byte sectors)
 constexpr int64_t kUnitMax = 4096;  // largest unit (compartments); larger cells are cut
 constexpr int64_t kPackAlign = 4;   // solver-layout blocks start on multiples of 4 compartments
 constexpr int64_t kTaskCompartments = 24576;  // default fill of a warp task
@@ -76,6 +89,6 @@ constexpr int64_t kMinTasks = 2048;           // smaller tasks for batches below
 
 // Return codes follow hines_status.
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,
-                    int sort_by_length, int pack_compartments, HostPlan& out);
+                    int sort_by_length, int pack_compartments, int pieces_per_lane, HostPlan& out);
 
 }  // namespace hines

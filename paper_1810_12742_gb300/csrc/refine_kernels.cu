@@ -1,13 +1,14 @@
-// FP32 elimination with FP64 residual refinement on the warp-task kernels
+// FP32 elimination with residual refinement on the warp-task kernels
 // (internal to libhines).
 //
 // x0 = A^{-1} b by the FP32 solve, which leaves the reciprocal eliminated
-// diagonal in the workspace; then, per step, the residual r = b - A x in FP64
-// (A and b the FP32 inputs widened exactly), the correction c = A^{-1} r by an
-// FP32 solve that re-uses that factor (only r is eliminated), and x += c in
-// FP64.  The residual of a compartment needs its parent and its children:
-// inside a branch those are the neighbouring compartments, at a branch's ends
-// the parent branch's last compartment and the child branches' first ones.
+// diagonal in the workspace; then, per step, one pass of the task kernels in
+// refinement mode: its elimination visit forms the residual r = b - A x
+// (exact products and error-free sums of the FP32 inputs, in FP32 words) and
+// eliminates it with the stored factor, its substitution visit solves for the
+// correction c and writes x + c (a double-float pair between steps, FP64
+// after the last).  The per-cell residual norms, when asked for, come from an
+// FP64 residual of the final x.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -91,28 +92,6 @@ __global__ void k_residual(DevPlan P, const float* __restrict__ d, const float* 
   }
 }
 
-// x += c in FP64, and per branch the largest |c|
-__global__ void k_update(DevPlan P, const float* __restrict__ c, double* __restrict__ x, double* __restrict__ bcorr) {
-  const int lane = threadIdx.x & 31, half = lane >> 4, t = lane & 15;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t nb = P.n_branches, pairs = (nb + 1) / 2;
-  for (int64_t pr = gw; pr < pairs; pr += nw) {
-    const int64_t br = 2 * pr + half;
-    const bool vb = br < nb;
-    const int len = vb ? P.br_len[br] : 0;
-    float cm = 0.f;  // |c| is an FP32 number: its maximum needs no FP64 instruction
-    if (t < len) {
-      const int64_t i = P.br_first[br] + t;
-      const float ci = c[i];
-      x[i] += widen(ci);
-      cm = fabsf(ci);
-    }
-    for (int o = 8; o > 0; o >>= 1) cm = fmaxf(cm, __shfl_xor_sync(kFull, cm, o));
-    if (vb && t == 0) bcorr[br] = cm;
-  }
-}
-
 __device__ __forceinline__ double warp_max(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
   return v;
@@ -120,13 +99,14 @@ __device__ __forceinline__ double warp_max(double v) {
 
 // One warp per cell: the cell's largest correction of this step from the
 // per-branch maxima; HINES_WARN_REFINE when it grew since the last step.
-__global__ void k_growth(DevPlan P, const double* __restrict__ bcorr, double* __restrict__ prev) {
+__global__ void k_growth(DevPlan P, const float* __restrict__ bcorr, double* __restrict__ prev) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = gw; c < P.n_cells; c += nw) {
     double m = 0.0;
-    for (int64_t br = P.cell_br_off[c] + lane; br < P.cell_br_off[c + 1]; br += 32) m = fmax(m, bcorr[br]);
+    for (int64_t br = P.cell_br_off[c] + lane; br < P.cell_br_off[c + 1]; br += 32)
+      m = fmax(m, widen(bcorr[br]));
     m = warp_max(m);
     if (lane == 0) {
       if (m > prev[c]) atomicMax(P.status, (int)HINES_WARN_REFINE);
@@ -171,27 +151,25 @@ cudaError_t launch_unit_refine(const DevPlan& P, const float* d, const float* u,
     if (relres && nc > 0) e = cudaMemsetAsync(relres, 0, (size_t)nc * sizeof(double), s);
     return e;
   }
-  float* xf = static_cast<float*>(P.fac) + (n > P.n_packed ? n : P.n_packed);  // after the FP32 factor
-  double* prev = static_cast<double*>(P.red);          // [n_cells] largest correction of the last step
-  double* bcorr = static_cast<double*>(P.cb);          // [nb] largest correction per branch
-  double* bstat = bcorr + P.n_branches;                // [nb][3] residual maxima per branch
+  float* x0 = static_cast<float*>(P.fac) + (n > P.n_packed ? n : P.n_packed);  // after the FP32 factor
+  double* prev = static_cast<double*>(P.red);  // [n_cells] largest correction of the last step
+  float* bcorr = static_cast<float*>(P.cb);    // [nb] largest correction per branch
+  double* bstat = static_cast<double*>(P.cb) + P.n_branches;  // [nb][3] residual maxima per branch
   const int blocks_b = grid_for(P, (P.n_branches + 1) / 2 * 32, 256);
   const int blocks_n = grid_for(P, n, 256);
   const int blocks_c = grid_for(P, (int64_t)nc * 32, 256);
-  e = cudaMemcpyAsync(xf, b, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = launch_unit_solve_f32(P, d, u, xf, s);
-  if (e == cudaSuccess) {
-    k_widen<<<blocks_n, 256, 0, s>>>(xf, x, n);
+  e = launch_unit_solve_f32_rhs(P, d, u, b, x0, s);
+  if (e == cudaSuccess && steps == 0) {
+    k_widen<<<blocks_n, 256, 0, s>>>(x0, x, n);
     e = cudaGetLastError();
   }
   // the "last step" maxima start huge, so that the first step never warns
-  if (e == cudaSuccess) e = cudaMemsetAsync(prev, 0x7F, (size_t)nc * sizeof(double), s);
-  for (int step = 0; step < steps && e == cudaSuccess; ++step) {
-    k_residual<false><<<blocks_b, 256, 0, s>>>(P, d, u, b, x, xf, nullptr);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = launch_unit_resolve_f32(P, u, xf, s);
+  if (e == cudaSuccess && steps > 0) e = cudaMemsetAsync(prev, 0x7F, (size_t)nc * sizeof(double), s);
+  for (int step = 1; step <= steps && e == cudaSuccess; ++step) {
+    const bool pairs = step > 1;  // after the first step x is a double-float pair, kept in x's 8 bytes
+    e = launch_unit_refine_step(P, d, u, b, pairs ? static_cast<const void*>(x) : static_cast<const void*>(x0), pairs,
+                                x, step == steps, bcorr, s);
     if (e != cudaSuccess) break;
-    k_update<<<blocks_b, 256, 0, s>>>(P, xf, x, bcorr);
     k_growth<<<blocks_c, 256, 0, s>>>(P, bcorr, prev);
     e = cudaGetLastError();
   }

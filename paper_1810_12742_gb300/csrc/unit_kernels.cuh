@@ -1,0 +1,1251 @@
+// Warp-task kernels of the batched Hines solver, sm_103a.
+//
+// The planner cuts every cell into units -- whole small cells, or the top part
+// and the subtrees of a large cell -- and packs units into tasks.  A warp owns
+// a task and walks its chunks (Hu's list schedule of the task's pieces, at
+// most 32 * P pieces each, longest first): deepest chunk first for the
+// elimination, root-side chunk first for the substitution (Section 3).  Lane
+// j owns the chunk's pieces P j .. P j + P - 1 (P = 1 or 2 pieces per lane).
+// Inside a piece the parent of compartment i is i - 1 (Section 5): the lane
+// runs a Thomas chain (Listing 1) and leaves one contribution for its parent
+// compartment (Listing 2's parent lookup).  With P = 2 the lane runs its two
+// chains at once, the two pieces aligned at their proximal ends (the shorter
+// one joins the chain when its distal row comes up), so that both halves of
+// every value live in one 8-byte register pair and the compensated
+// arithmetic runs on packed FP32-pair instructions.
+//
+// A solve is two launches: (A) whole-cell tasks (both sweeps), the
+// elimination of subtree tasks and, taken over by the warp that finishes a
+// cell's last subtree, that cell's top part (both sweeps); (C) the
+// substitution of subtree tasks.  No warp ever waits for another.
+//
+// The chunks of a task follow one another in the same warp, so a chunk's
+// children are usually in the chunk just before it (elimination) and its
+// parents likewise (substitution): those values pass through a small shared
+// memory cache; other values go through global memory.  A chunk's inputs are
+// staged with cp.async into shared memory in the row layout of Section 5
+// (row r: the compartments r rows from each pair's distal start, one word per
+// piece), so that a lane reads its P values of a row as one word.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/hines.h"
+#include "device_common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+namespace hines {
+namespace {
+
+using namespace dev;
+
+constexpr int kL = kBranchCap;          // rows (compartments per piece), at most
+constexpr int kWarps = kWarpsPerCta;
+constexpr int kSmemPerSm = 227 * 1024;  // shared memory one SM gives its CTAs
+
+template <int P>
+struct Geo {
+  static constexpr int kChunk = 32 * P;              // pieces per chunk
+  static constexpr int kS = P == 2 ? 66 : 32;        // natural staging: words per row
+  static constexpr int kSlots = kL * kS + 4;         // words per staged array (holds a padded solver-layout block)
+};
+// Natural-layout staging: the word of piece i's compartment in row r.  One
+// piece per lane: rows of 32 words, the column XOR-swizzled by the row, so
+// that the warp's staging copies (sixteen consecutive rows of one piece per
+// half-warp) and the lanes' row reads are both free of bank conflicts.  Two
+// pieces per lane: rows of 66 words (64 + 2), so that a lane's pair is one
+// aligned 8-byte word and the staging copies spread over the banks.
+template <int P>
+__device__ __forceinline__ int nidx(int r, int i) {
+  if constexpr (P == 2)
+    return r * 66 + i;
+  else
+    return (r << 5) + (i ^ (r & 31));
+}
+template <int P>
+struct VOf {
+  using type = float;
+};
+template <>
+struct VOf<2> {
+  using type = F2;
+};
+
+// ---- per-lane metadata ------------------------------------------------------
+struct Piece {
+  long long first, pcomp;  // natural: proximal compartment, parent compartment; solver layout: the chunk's
+                           // block offset, the parent's solver-layout index (-1 at a cell's root)
+  int ppos, cpos, len, nchild, ccontig, xtask;
+};
+template <int P>
+struct Meta {
+  Piece p[P];
+  float4 ds[P];  // compensated substitution: folded distal state left by the elimination
+  int L;         // rows of the lane: length of its first (longer) piece, 0 for a lane without pieces
+};
+
+template <bool kPk, int P>
+__device__ __forceinline__ Meta<P> load_meta(const DevPlan& Pl, int c0, int n, int lane, bool active, bool want_ds) {
+  Meta<P> m;
+#pragma unroll
+  for (int h = 0; h < P; ++h) {
+    const int i = P * lane + h;
+    Piece q{0, -1, -1, 0, 0, 0, 0, 0};
+    m.ds[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (active && i < n) {
+      const int pos = c0 + i;
+      if (want_ds) m.ds[h] = static_cast<const float4*>(Pl.dstate)[pos];
+      const BrMetaT t = Pl.tmeta[pos];
+      if (kPk) {
+        const longlong2 w = Pl.pk_meta[pos];
+        q.first = w.x;
+        q.pcomp = w.y;
+      } else {
+        q.first = t.first;
+        q.pcomp = t.pcomp;
+      }
+      q.ppos = t.ppos;
+      q.cpos = t.cpos;
+      q.len = t.len;
+      q.nchild = t.nchild;
+      q.ccontig = t.ccontig;
+      q.xtask = t.xtask;
+    }
+    m.p[h] = q;
+  }
+  m.L = m.p[0].len;
+  return m;
+}
+
+__device__ __forceinline__ int child_pos(const DevPlan& Pl, const Piece& q, int c) {
+  return q.ccontig ? q.cpos + c : __ldg(Pl.tchild + q.cpos + c);
+}
+
+// A child's contribution slot: through L2 when another warp may have written
+// it in this launch (a top part's subtree children), else the ordinary path.
+template <typename W>
+__device__ __forceinline__ W slot_load(const W* p, const Piece& q) {
+  return q.xtask ? __ldcg(p) : *p;
+}
+
+// The chunk processed just before the current one in the same sweep.
+struct Prev {
+  int c0, n, which;  // n = 0: none
+};
+
+// ---- rows of the staged chunk -------------------------------------------------
+// Word index of row r's first slot: natural layout, the fixed stride of the
+// staging buffer; solver layout, the block's row offsets (a per-warp table).
+template <bool kPk, int P>
+struct Rows {
+  const int* tab;
+  // word of chunk position j (a lane's first piece: P * lane) in row r
+  __device__ __forceinline__ int slot(int r, int j) const {
+    if constexpr (kPk)
+      return tab[r] + j;
+    else
+      return nidx<P>(r, j);
+  }
+};
+
+// Solver layout: the row offsets of the current chunk's block from the lanes'
+// row counts (every lane calls it); tab[kL] is the block's slot count.
+template <int P>
+__device__ __forceinline__ void build_row_table(int L, int lane, int* tab) {
+  int acc = 0;
+#pragma unroll
+  for (int r = 0; r < kL; ++r) {
+    const int nl = __popc(__ballot_sync(kFull, L > r));
+    if (lane == r) tab[r] = acc;
+    acc += P * nl;
+  }
+  if (lane == 0) tab[kL] = acc;
+  __syncwarp();
+}
+
+// Every element of the chunk's pieces in the natural layout: sixteen lanes
+// per piece, two pieces per step (pieces are at most 16 long); the owner
+// lane's metadata comes by shuffle.  f(i, t, row, g, root) for piece i,
+// distance t from its proximal end, row of the staged chunk, natural index g,
+// and whether the piece holds its cell's root compartment (its parent is none).
+template <int P, typename F>
+__device__ __forceinline__ void for_chunk_elements(const Meta<P>& m, int n, int lane, F&& f) {
+  const int half = lane >> 4, t = lane & 15;
+  for (int j = 0; j < n; j += 2) {
+    const int i = j + half, src = (i / P) & 31;
+    long long first = __shfl_sync(kFull, m.p[0].first, src);
+    int len = __shfl_sync(kFull, m.p[0].len, src);
+    int root = __shfl_sync(kFull, (int)(m.p[0].pcomp < 0), src);
+    const int rows = P == 2 ? __shfl_sync(kFull, m.L, src) : len;
+    if constexpr (P == 2) {
+      const long long f1 = __shfl_sync(kFull, m.p[1].first, src);
+      const int l1 = __shfl_sync(kFull, m.p[1].len, src);
+      const int r1 = __shfl_sync(kFull, (int)(m.p[1].pcomp < 0), src);
+      if (i & 1) {
+        first = f1;
+        len = l1;
+        root = r1;
+      }
+    }
+    if (i < n && t < len) f(i, t, rows - 1 - t, first + t, root != 0);
+  }
+}
+
+// Solver layout: copy the chunk's block of one array into shared memory with
+// 16-byte copies (blocks start on multiples of 4 slots and are padded).
+template <typename T>
+__device__ __forceinline__ void stage_block(T* dst, const T* src, long long blk, int e, int lane) {
+  constexpr int V = 16 / (int)sizeof(T);
+  const int nv = (e + V - 1) / V;
+  for (int v = lane; v < nv; v += 32) cp_async16(dst + v * V, src + blk + (long long)v * V);
+}
+
+// ---- one or two values of a row -------------------------------------------------
+__device__ __forceinline__ float ldv(const float* s, int idx, float) { return s[idx]; }
+__device__ __forceinline__ F2 ldv(const float* s, int idx, F2) { return *reinterpret_cast<const F2*>(s + idx); }
+__device__ __forceinline__ void stv(float* s, int idx, float v) { s[idx] = v; }
+__device__ __forceinline__ void stv(float* s, int idx, F2 v) { *reinterpret_cast<F2*>(s + idx) = v; }
+__device__ __forceinline__ float vget(float v, int) { return v; }
+__device__ __forceinline__ float vget(F2 v, int h) { return h == 0 ? f2_lo(v) : f2_hi(v); }
+template <int P>
+__device__ __forceinline__ typename VOf<P>::type vpack(const float* a) {
+  if constexpr (P == 2)
+    return f2_make(a[0], a[1]);
+  else
+    return a[0];
+}
+// the second half of v replaced by w (the shorter piece joins its chain)
+__device__ __forceinline__ F2 vset_hi(F2 v, float w) { return f2_make(f2_lo(v), w); }
+
+// ============================================================================
+// Compensated mode: FP32 inputs, double-float arithmetic from FP32 error-free
+// transformations, FP64 solution.  The elimination keeps nothing per
+// compartment: it leaves, per piece, its contribution to the parent (or the
+// root's solution) and its folded distal state; the substitution re-stages the
+// chunk and re-eliminates it from that state before substituting.
+// ============================================================================
+template <bool kPk, int P>
+struct CompMode {
+  using V = typename VOf<P>::type;
+  using G = Geo<P>;
+  static constexpr bool kPacked = kPk;
+  static constexpr int kPer = P;
+  struct Args {
+    const float* d;
+    const float* u;
+    const float* b;
+    double* x;
+  };
+  // a staging buffer: d, u, b, then the chunk's row table (solver layout)
+  static constexpr int kTab = 3 * G::kSlots * 4;
+  static constexpr int kStageBytes = kTab + 80;
+  // two buffers with one piece per lane (the next chunk is staged while this
+  // one is computed); one with two, whose chunks are twice as large
+  static constexpr int kStages = P == 1 ? 2 : 1;
+  static constexpr int kCslot = 0, kCx = 2 * G::kChunk * 16;
+  static constexpr int kCacheBytes = kCx + 2 * G::kChunk * 8;
+  static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
+  // CTAs per SM that shared memory allows; two pieces per lane need more
+  // registers than eight CTAs leave, so they are held to six
+  static constexpr int kMinBlocks = P == 2 ? 6 : kSmemPerSm / (kWarps * kWarpBytes);
+  static constexpr bool kWantDs = true;
+
+  __device__ static void stage(const DevPlan&, const Args& A, int, const Meta<P>& m, int n, int lane,
+                               unsigned char* buf) {
+    float* sd = reinterpret_cast<float*>(buf);
+    float* su = sd + G::kSlots;
+    float* sb = su + G::kSlots;
+    if (kPk) {
+      int* tab = reinterpret_cast<int*>(buf + kTab);
+      build_row_table<P>(m.L, lane, tab);
+      const long long blk = __shfl_sync(kFull, m.p[0].first, 0);
+      const int e = tab[kL];
+      stage_block(sd, A.d, blk, e, lane);
+      stage_block(su, A.u, blk, e, lane);
+      stage_block(sb, A.b, blk, e, lane);
+    } else {
+      for_chunk_elements(m, n, lane, [&](int i, int, int row, long long g, bool) {
+        const int q = nidx<P>(row, i);
+        cp_async4(&sd[q], A.d + g);
+        cp_async4(&su[q], A.u + g);
+        cp_async4(&sb[q], A.b + g);
+      });
+    }
+    cp_commit();
+  }
+
+  __device__ static void compute(const DevPlan& Pl, const Args&, int visit, int c0, int n, int lane,
+                                 const Meta<P>& m, unsigned char* buf, const Prev& pv, unsigned char* cache, int cur) {
+    float* sd = reinterpret_cast<float*>(buf);
+    float* su = sd + G::kSlots;
+    float* sb = su + G::kSlots;
+    float4* cslot = reinterpret_cast<float4*>(cache + kCslot);  // [2][kChunk] contributions
+    float2* cx = reinterpret_cast<float2*>(cache + kCx);        // [2][kChunk] distal solutions
+    const Rows<kPk, P> rows{reinterpret_cast<const int*>(buf + kTab)};
+    float4* slot = static_cast<float4*>(Pl.cd);
+    float4* dst = static_cast<float4*>(Pl.dstate);
+    float2* xlast = static_cast<float2*>(Pl.xlast);
+    const int L = m.L;
+    if (L == 0) return;
+    const int me = P * lane;
+    // the second piece's distal row (it joins the chain there); L: none
+    const int delta = P == 2 ? L - m.p[P - 1].len : 0;
+    float d0h[P], d0l[P], b0h[P], b0l[P];
+    if (visit == 0) {
+#pragma unroll
+      for (int h = 0; h < P; ++h) {
+        const Piece& q = m.p[h];
+        d0h[h] = 1.f;
+        d0l[h] = b0h[h] = b0l[h] = 0.f;
+        if (q.len == 0) continue;
+        const int idx = rows.slot(L - q.len, me + h);
+        ff Dv = {sd[idx], 0.f}, Bv = {sb[idx], 0.f};
+        for (int c = 0; c < q.nchild; ++c) {
+          const int cp = child_pos(Pl, q, c);
+          const int loc = cp - pv.c0;
+          const float4 v = (loc >= 0 && loc < pv.n) ? cslot[pv.which * G::kChunk + loc] : slot_load(slot + cp, q);
+          Dv = ff_sub(Dv, v.x, v.y);
+          Bv = ff_sub(Bv, v.z, v.w);
+        }
+        dst[c0 + me + h] = make_float4(Dv.h, Dv.l, Bv.h, Bv.l);
+        d0h[h] = Dv.h;
+        d0l[h] = Dv.l;
+        b0h[h] = Bv.h;
+        b0l[h] = Bv.l;
+      }
+      FFV<V> D{vpack<P>(d0h), vpack<P>(d0l)}, B{vpack<P>(b0h), vpack<P>(b0l)};
+#pragma unroll
+      for (int r = 1; r < kL; ++r) {
+        if (r < L) {
+          const int i0 = rows.slot(r - 1, me), i1 = rows.slot(r, me);
+          const V uk = ldv(su, i0, V{});
+          const FFV<V> f = vdiv_f(uk, D);
+          const FFV<V> fu = vmul_f(f, uk);
+          const FFV<V> fb = vmul_ff(f, B);
+          D = vsub_dom(ldv(sd, i1, V{}), fu.h, fu.l);
+          B = vsub_ff(ldv(sb, i1, V{}), fb.h, fb.l);
+          if constexpr (P == 2) {
+            if (r == delta) {
+              D = {vset_hi(D.h, d0h[1]), vset_hi(D.l, d0l[1])};
+              B = {vset_hi(B.h, b0h[1]), vset_hi(B.l, b0l[1])};
+            }
+          }
+        }
+      }
+      // the proximal row: contribution to the parent, or the root's solution
+      const V uk = ldv(su, rows.slot(L - 1, me), V{});
+      const FFV<V> f = vdiv_f(uk, D);
+      const FFV<V> fu = vmul_f(f, uk);
+      const FFV<V> fb = vmul_ff(f, B);
+      const FFV<V> x0 = vdiv(B, D);
+#pragma unroll
+      for (int h = 0; h < P; ++h) {
+        if (m.p[h].len == 0) continue;
+        const float4 out = m.p[h].pcomp >= 0
+                               ? make_float4(vget(fu.h, h), vget(fu.l, h), vget(fb.h, h), vget(fb.l, h))
+                               : make_float4(vget(x0.h, h), vget(x0.l, h), 0.f, 0.f);
+        slot[c0 + me + h] = out;
+        cslot[cur * G::kChunk + me + h] = out;
+      }
+      return;
+    }
+    // substitution: re-eliminate from the folded distal state, keeping the
+    // pivots' and right-hand sides' high parts in the staged rows and their
+    // low parts in registers, then substitute from the proximal row
+#pragma unroll
+    for (int h = 0; h < P; ++h) {
+      d0h[h] = m.ds[h].x;
+      d0l[h] = m.ds[h].y;
+      b0h[h] = m.ds[h].z;
+      b0l[h] = m.ds[h].w;
+    }
+    FFV<V> D{vpack<P>(d0h), vpack<P>(d0l)}, B{vpack<P>(b0h), vpack<P>(b0l)};
+    V Dl[kL], Bl[kL];
+    {
+      const int i0 = rows.slot(0, me);
+      stv(sd, i0, D.h);
+      stv(sb, i0, B.h);
+      Dl[0] = D.l;
+      Bl[0] = B.l;
+    }
+#pragma unroll
+    for (int r = 1; r < kL; ++r) {
+      if (r < L) {
+        const int i0 = rows.slot(r - 1, me), i1 = rows.slot(r, me);
+        const V uk = ldv(su, i0, V{});
+        const FFV<V> f = vdiv_f(uk, D);
+        const FFV<V> fu = vmul_f(f, uk);
+        const FFV<V> fb = vmul_ff(f, B);
+        D = vsub_dom(ldv(sd, i1, V{}), fu.h, fu.l);
+        B = vsub_ff(ldv(sb, i1, V{}), fb.h, fb.l);
+        if constexpr (P == 2) {
+          if (r == delta) {
+            D = {vset_hi(D.h, d0h[1]), vset_hi(D.l, d0l[1])};
+            B = {vset_hi(B.h, b0h[1]), vset_hi(B.l, b0l[1])};
+          }
+        }
+        stv(sd, i1, D.h);
+        stv(sb, i1, B.h);
+        Dl[r] = D.l;
+        Bl[r] = B.l;
+      }
+    }
+    // the parents' distal solutions (a cell's root: none; its coupling is not
+    // part of the system, so it is taken as zero)
+    float xph[P], xpl[P];
+#pragma unroll
+    for (int h = 0; h < P; ++h) {
+      const Piece& q = m.p[h];
+      xph[h] = xpl[h] = 0.f;
+      if (q.len > 0 && q.pcomp >= 0) {
+        const int loc = q.ppos - pv.c0;
+        const float2 t = (loc >= 0 && loc < pv.n) ? cx[pv.which * G::kChunk + loc] : xlast[q.ppos];
+        xph[h] = t.x;
+        xpl[h] = t.y;
+      } else if (q.len > 0) {
+        su[rows.slot(L - 1, me + h)] = 0.f;
+      }
+    }
+    FFV<V> X{vpack<P>(xph), vpack<P>(xpl)};
+    float xbh = 0.f, xbl = 0.f;  // the second piece's distal solution
+#pragma unroll
+    for (int r = kL - 1; r >= 0; --r) {
+      if (r < L) {
+        const int i = rows.slot(r, me);
+        const V uk = ldv(su, i, V{});
+        const FFV<V> M = vmul_f(X, uk);
+        const FFV<V> num = vsub_ffff(FFV<V>{ldv(sb, i, V{}), Bl[r]}, M.h, M.l);
+        X = vdiv(num, FFV<V>{ldv(sd, i, V{}), Dl[r]});
+        if constexpr (P == 2) {
+          reinterpret_cast<double*>(sd + i)[0] = ff_to_double(f2_lo(X.h), f2_lo(X.l));
+          reinterpret_cast<double*>(sb + i)[0] = ff_to_double(f2_hi(X.h), f2_hi(X.l));
+          if (r == delta) {
+            xbh = f2_hi(X.h);
+            xbl = f2_hi(X.l);
+          }
+        } else {
+          const double xd = ff_to_double(X.h, X.l);
+          sd[i] = __int_as_float(__double2loint(xd));
+          sb[i] = __int_as_float(__double2hiint(xd));
+        }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < P; ++h) {
+      if (m.p[h].len == 0) continue;
+      const float2 xo = h == 0 ? make_float2(vget(X.h, 0), vget(X.l, 0)) : make_float2(xbh, xbl);
+      xlast[c0 + me + h] = xo;
+      cx[cur * G::kChunk + me + h] = xo;
+    }
+  }
+
+  // the FP64 solution of a staged slot (natural layout: piece i at row r)
+  __device__ static double x_at(const float* sd, const float* sb, int q) {
+    if constexpr (P == 2) {
+      return (q & 1) ? reinterpret_cast<const double*>(sb + q - 1)[0] : reinterpret_cast<const double*>(sd + q)[0];
+    } else {
+      return __hiloint2double(__float_as_int(sb[q]), __float_as_int(sd[q]));
+    }
+  }
+
+  __device__ static void copy_out(const DevPlan&, const Args& A, int visit, const Meta<P>& m, int n, int lane,
+                                  unsigned char* buf) {
+    if (visit == 0) return;
+    const float* sd = reinterpret_cast<const float*>(buf);
+    const float* sb = sd + 2 * G::kSlots;
+    if (kPk) {
+      const int* tab = reinterpret_cast<const int*>(buf + kTab);
+      const long long blk = __shfl_sync(kFull, m.p[0].first, 0);
+      const int e = tab[kL];
+      for (int s = lane; s < e; s += 32) A.x[blk + s] = x_at(sd, sb, s);
+      return;
+    }
+    for_chunk_elements(m, n, lane,
+                       [&](int i, int, int row, long long g, bool) { A.x[g] = x_at(sd, sb, nidx<P>(row, i)); });
+  }
+};
+
+// ============================================================================
+// Factor mode (FP64, FP32, passive cable): the elimination writes the
+// reciprocal eliminated diagonal to the workspace and the eliminated
+// right-hand side in place; the substitution reads them back.  In cable mode
+// the system is rebuilt while staging (Section 1's implicit-Euler system):
+// d_i = s_i (1 + theta dt g_i) + sum of a over the edges at i (a = -u),
+// b_i = s_i V_i + s_i dt g_i (E - (1 - theta) V_i).
+// The lane's pieces are handled one after the other in the same loop step
+// (no packed FP64 instructions exist), their rows aligned as in the compensated
+// mode; a piece's rows before its distal row are skipped.
+// ============================================================================
+// kReuse: the elimination of a new right-hand side with the factor a previous
+// solve of the same plan and matrix left in the workspace (the reciprocal
+// eliminated diagonal): only b is eliminated (the refinement's correction
+// solves; passive-cable steps after the first, the matrix being constant).
+template <typename T, bool kCable, bool kPk, int P, bool kReuse = false>
+struct FactorMode {
+  using G = Geo<P>;
+  // the reciprocal eliminated diagonal: FP64 as rcp_t gives it; FP32 with one
+  // more Newton step on the hardware approximation, so that the stored factor
+  // is that of an FP32 elimination to the last bit or so, which the
+  // refinement's re-solves depend on
+  __device__ static T rcp_solve(T x) {
+    T r = rcp_t(x);
+    if (sizeof(T) == 4) r = fma(r, fma(-x, r, T(1)), r);
+    return r;
+  }
+  static constexpr bool kPacked = kPk;
+  static constexpr int kPer = P;
+  struct Args {
+    const T* d;
+    const T* u;
+    const T* s;  // cable: s, g
+    const T* g;
+    T* x;        // right-hand side in, solution out (cable: V in, V out)
+    T dt, E, theta;
+    bool rhs_from_V;
+    const T* rhs = nullptr;  // non-null: the right-hand side is read from here (x receives the solution)
+  };
+  // a staging buffer: d (or the factor), u, b, then the row table (solver layout)
+  static constexpr int kTab = 3 * G::kSlots * (int)sizeof(T);
+  static constexpr int kStageBytes = kTab + 80;
+  // FP64 chunks are large and the FP64 pipe is slow: one staging buffer, so
+  // that more warps share an SM; FP32 with one piece per lane: two
+  static constexpr int kStages = (sizeof(T) == 4 && P == 1) ? 2 : 1;
+  static constexpr int kCslot = 0, kCx = 2 * G::kChunk * 2 * (int)sizeof(T);
+  static constexpr int kCacheBytes = kCx + 2 * G::kChunk * (int)sizeof(T);
+  static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
+  static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);
+  static constexpr bool kWantDs = false;
+
+  // Section 1's implicit-Euler system: the membrane part of the diagonal,
+  // s (1 + theta dt g), and the right-hand side s (V + dt g (E - (1 - theta) V)),
+  // each in the fewest operations (theta = 1: s (V + dt E g))
+  __device__ static T cable_diag(const Args& A, T si, T gi) { return si * fma(A.theta * A.dt, gi, T(1)); }
+  __device__ static T cable_rhs(const Args& A, T si, T gi, T vi) {
+    if (A.theta == T(1)) return si * fma(A.dt * A.E, gi, vi);
+    return si * fma(A.dt * gi, fma(A.theta - T(1), vi, A.E), vi);
+  }
+
+  __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, const Meta<P>& m, int n, int lane,
+                               unsigned char* buf) {
+    T* sd = reinterpret_cast<T*>(buf);
+    T* su = sd + G::kSlots;
+    T* sb = su + G::kSlots;
+    const T* fac = static_cast<const T*>(Pl.fac);
+    if (kPk) {
+      int* tab = reinterpret_cast<int*>(buf + kTab);
+      build_row_table<P>(m.L, lane, tab);
+      const long long blk = __shfl_sync(kFull, m.p[0].first, 0);
+      const int e = tab[kL];
+      if (kCable && visit == 0) {
+        // the block's rows in place; the own edge to the parent is taken off
+        // the diagonal in compute(), where the cell's root compartment is known
+        if (kReuse) {  // the stored factor; only the right-hand side is rebuilt
+          stage_block(sd, fac, blk, e, lane);
+          stage_block(su, A.u, blk, e, lane);
+        }
+        for (int i = lane; i < e; i += 32) {
+          const long long g = blk + i;
+          const T vi = A.x[g];
+          if (kReuse) {
+            sb[i] = A.rhs_from_V ? cable_rhs(A, A.s[g], A.g[g], vi) : vi;
+          } else {
+            const T si = A.s[g], gi = A.g[g], ui = A.u[g];
+            sd[i] = cable_diag(A, si, gi);
+            su[i] = ui;
+            sb[i] = A.rhs_from_V ? cable_rhs(A, si, gi, vi) : vi;
+          }
+        }
+      } else {
+        stage_block(sd, (visit == 1 || kReuse) ? fac : A.d, blk, e, lane);
+        stage_block(su, A.u, blk, e, lane);
+        stage_block(sb, (visit == 0 && A.rhs) ? A.rhs : static_cast<const T*>(A.x), blk, e, lane);
+      }
+      cp_commit();
+      return;
+    }
+    if (visit == 1 || !kCable) {
+      const T* dsrc = (visit == 1 || kReuse) ? fac : A.d;
+      const T* bsrc = (visit == 0 && A.rhs) ? A.rhs : A.x;
+      for_chunk_elements(m, n, lane, [&](int i, int, int row, long long g, bool) {
+        const int q = nidx<P>(row, i);
+        cp_async(&sd[q], dsrc + g);
+        cp_async(&su[q], A.u + g);
+        cp_async(&sb[q], bsrc + g);
+      });
+    } else if (kReuse) {  // cable, stored factor: only the right-hand side is rebuilt
+      for_chunk_elements(m, n, lane, [&](int i, int, int row, long long g, bool) {
+        const int q = nidx<P>(row, i);
+        cp_async(&sd[q], fac + g);
+        cp_async(&su[q], A.u + g);
+        const T vi = A.x[g];
+        sb[q] = A.rhs_from_V ? cable_rhs(A, A.s[g], A.g[g], vi) : vi;
+      });
+    } else {
+      // the own edge to the parent comes off every diagonal but a cell root's
+      for_chunk_elements(m, n, lane, [&](int i, int t, int row, long long g, bool root) {
+        const T si = A.s[g], gi = A.g[g], ui = A.u[g], vi = A.x[g];
+        T dd = cable_diag(A, si, gi);
+        if (!(root && t == 0)) dd -= ui;  // own edge to the parent
+        const int q = nidx<P>(row, i);
+        sd[q] = dd;
+        su[q] = ui;
+        sb[q] = A.rhs_from_V ? cable_rhs(A, si, gi, vi) : vi;
+      });
+    }
+    cp_commit();
+  }
+
+  __device__ static void compute(const DevPlan& Pl, const Args& A, int visit, int c0, int n, int lane,
+                                 const Meta<P>& m, unsigned char* buf, const Prev& pv, unsigned char* cache, int cur) {
+    T* sd = reinterpret_cast<T*>(buf);
+    T* su = sd + G::kSlots;
+    T* sb = su + G::kSlots;
+    T* cslot = reinterpret_cast<T*>(cache + kCslot);  // [2][kChunk][2] contributions
+    T* cx = reinterpret_cast<T*>(cache + kCx);        // [2][kChunk] distal solutions
+    T* slot = static_cast<T*>(Pl.cd);                 // [nb][2]
+    const Rows<kPk, P> rows{reinterpret_cast<const int*>(buf + kTab)};
+    const int L = m.L;
+    if (L == 0) return;
+    const int me = P * lane;
+    int first_row[P];  // each piece's distal row
+#pragma unroll
+    for (int h = 0; h < P; ++h) first_row[h] = m.p[h].len > 0 ? L - m.p[h].len : kL;
+    if (visit == 0) {
+      if (kPk && kCable && !kReuse) {
+        // solver layout: own edge to the parent, except at a cell's root
+        // compartment (the proximal compartment of a root piece, row L - 1)
+#pragma unroll
+        for (int r = 0; r < kL; ++r) {
+          if (r < L) {
+#pragma unroll
+            for (int h = 0; h < P; ++h) {
+              if (r >= first_row[h] && !(m.p[h].pcomp < 0 && r == L - 1)) {
+                const int i = rows.slot(r, me + h);
+                sd[i] -= su[i];
+              }
+            }
+          }
+        }
+      }
+      T D[P], B[P];
+#pragma unroll
+      for (int h = 0; h < P; ++h) {
+        const Piece& q = m.p[h];
+        D[h] = T(1);
+        B[h] = T(0);
+        if (q.len == 0) continue;
+        const int idx = rows.slot(first_row[h], me + h);
+        if (!kReuse) D[h] = sd[idx];
+        B[h] = sb[idx];
+        for (int c = 0; c < q.nchild; ++c) {
+          const int cp = child_pos(Pl, q, c);
+          const int loc = cp - pv.c0;
+          const bool local = loc >= 0 && loc < pv.n;
+          if (!kReuse) D[h] -= local ? cslot[(pv.which * G::kChunk + loc) * 2] : slot_load(slot + 2 * cp, q);
+          B[h] -= local ? cslot[(pv.which * G::kChunk + loc) * 2 + 1] : slot_load(slot + 2 * cp + 1, q);
+        }
+      }
+      // rows from the distal end: store the reciprocal pivot (or, reusing the
+      // factor, read it) and the eliminated right-hand side, then pass the
+      // chain on; at the proximal row leave the contribution to the parent
+      T c0v[P], c1v[P];
+#pragma unroll
+      for (int h = 0; h < P; ++h) c0v[h] = c1v[h] = T(0);
+#pragma unroll
+      for (int r = 0; r < kL; ++r) {
+        if (r < L) {
+          const int i = rows.slot(r, me);
+#pragma unroll
+          for (int h = 0; h < P; ++h) {
+            if (r < first_row[h]) continue;
+            const T uk = su[i + h];
+            const T rr = kReuse ? sd[i + h] : rcp_solve(D[h]);
+            if (!kReuse) sd[i + h] = rr;
+            const T f = uk * rr;
+            if (r < L - 1) {
+              sb[i + h] = B[h];
+              const int i1 = rows.slot(r + 1, me + h);
+              if (!kReuse) {
+                D[h] = sd[i1] - f * uk;
+                if (kCable) D[h] -= uk;  // the edge to the chain child
+              }
+              B[h] = sb[i1] - f * B[h];
+            } else if (m.p[h].pcomp >= 0) {
+              sb[i + h] = B[h];
+              c0v[h] = kReuse ? T(0) : (kCable ? f * uk + uk : f * uk);
+              c1v[h] = f * B[h];
+            } else {
+              sb[i + h] = B[h] * rr;  // solve root
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < P; ++h) {
+        if (m.p[h].len == 0) continue;
+        const int pos = c0 + me + h;
+        slot[2 * pos] = c0v[h];
+        slot[2 * pos + 1] = c1v[h];
+        cslot[(cur * G::kChunk + me + h) * 2] = c0v[h];
+        cslot[(cur * G::kChunk + me + h) * 2 + 1] = c1v[h];
+      }
+      return;
+    }
+    T xp[P];
+#pragma unroll
+    for (int h = 0; h < P; ++h) {
+      const Piece& q = m.p[h];
+      xp[h] = T(0);
+      if (q.len > 0 && q.pcomp >= 0) {
+        const int loc = q.ppos - pv.c0;
+        xp[h] = (loc >= 0 && loc < pv.n) ? cx[pv.which * G::kChunk + loc] : A.x[q.pcomp];
+      }
+    }
+#pragma unroll
+    for (int r = kL - 1; r >= 0; --r) {
+      if (r < L) {
+        const int i = rows.slot(r, me);
+#pragma unroll
+        for (int h = 0; h < P; ++h) {
+          if (r < first_row[h]) continue;
+          const T xi = (m.p[h].pcomp < 0 && r == L - 1) ? sb[i + h] : (sb[i + h] - su[i + h] * xp[h]) * sd[i + h];
+          sb[i + h] = xi;
+          xp[h] = xi;
+        }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < P; ++h)
+      if (m.p[h].len > 0) cx[cur * G::kChunk + me + h] = xp[h];
+  }
+
+  __device__ static void copy_out(const DevPlan& Pl, const Args& A, int visit, const Meta<P>& m, int n, int lane,
+                                  unsigned char* buf) {
+    const T* sd = reinterpret_cast<const T*>(buf);
+    const T* sb = sd + 2 * G::kSlots;
+    T* fac = static_cast<T*>(Pl.fac);
+    if (kPk) {
+      const int* tab = reinterpret_cast<const int*>(buf + kTab);
+      const long long blk = __shfl_sync(kFull, m.p[0].first, 0);
+      const int e = tab[kL];
+      for (int s = lane; s < e; s += 32) {
+        if (visit == 0 && !kReuse) fac[blk + s] = sd[s];
+        A.x[blk + s] = sb[s];
+      }
+      return;
+    }
+    for_chunk_elements(m, n, lane, [&](int i, int, int row, long long g, bool) {
+      const int q = nidx<P>(row, i);
+      if (visit == 0 && !kReuse) fac[g] = sd[q];
+      A.x[g] = sb[q];
+    });
+  }
+};
+
+// ============================================================================
+// Refinement mode (natural layout): one step of iterative refinement on the
+// FP32 factor that a FactorMode<float> solve of the same plan left in the
+// workspace (the reciprocal pivots).  The elimination visit forms the
+// residual r = b - A x of the current x (the FP32 inputs taken exactly;
+// products and sums by error-free transformations, so that r keeps FP32
+// accuracy although it is tiny next to b) and eliminates it with the stored
+// factor, as the FP32 solve eliminated b.  A compartment's residual needs its
+// parent's x (the next row; at the proximal row, the parent piece's distal
+// compartment) and its children's (the previous row; at a piece's distal
+// row, the child pieces pass their products u x up with their
+// contributions).  The substitution visit solves for the correction c with
+// the same factor and writes x + c.  kIn: x is FP32 (0) or a double-float
+// pair (1); kOut: x + c as a pair (0, for another step) or in FP64 (1).
+// ============================================================================
+template <int P, int kIn, int kOut>
+struct RefineMode {
+  using V = typename VOf<P>::type;
+  using G = Geo<P>;
+  static constexpr bool kPacked = false;
+  static constexpr int kPer = P;
+  struct Args {
+    const float* d;
+    const float* u;
+    const float* b;
+    const void* x;     // kIn 0: float[n]; 1: float2[n]
+    float* rw;         // the eliminated residual (the correction's right-hand side)
+    void* xo;          // kOut 0: float2[n]; 1: double[n]
+    float* bcorr;      // per piece (branch id): largest |c| of this step
+  };
+  // staged words: d, u, b (visit 1: the eliminated residual), the factor, and
+  // x as pairs (two words per slot; FP32 x uses the first)
+  static constexpr int kTab = 6 * G::kSlots * 4;
+  static constexpr int kStageBytes = kTab + 80;
+  static constexpr int kStages = 1;
+  static constexpr int kCslot = 0, kCx = 2 * G::kChunk * 16;
+  static constexpr int kCacheBytes = kCx + 2 * G::kChunk * 8;
+  static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
+  static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);
+  static constexpr bool kWantDs = false;
+
+  __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, const Meta<P>& m, int n, int lane,
+                               unsigned char* buf) {
+    float* sd = reinterpret_cast<float*>(buf);
+    float* su = sd + G::kSlots;
+    float* sb = su + G::kSlots;
+    float* sf = sb + G::kSlots;
+    float* sx = sf + G::kSlots;  // [2 * kSlots]
+    const float* fac = static_cast<const float*>(Pl.fac);
+    for_chunk_elements(m, n, lane, [&](int i, int, int row, long long g, bool) {
+      const int q = nidx<P>(row, i);
+      if (visit == 0) {
+        cp_async4(&sd[q], A.d + g);
+        cp_async4(&sb[q], A.b + g);
+      } else {
+        cp_async4(&sb[q], A.rw + g);
+      }
+      cp_async4(&su[q], A.u + g);
+      cp_async4(&sf[q], fac + g);
+      if (kIn == 1)
+        cp_async8(&sx[2 * q], static_cast<const float2*>(A.x) + g);
+      else
+        cp_async4(&sx[2 * q], static_cast<const float*>(A.x) + g);
+    });
+    cp_commit();
+  }
+
+  // x of a row: the lane's P values as a double-float pair
+  __device__ static FFV<V> ldx(const float* sx, int idx) {
+    if constexpr (P == 2) {
+      const float4 v = *reinterpret_cast<const float4*>(sx + 2 * idx);
+      return {f2_make(v.x, v.z), kIn == 1 ? f2_make(v.y, v.w) : f2_make(0.f, 0.f)};
+    } else {
+      const float2 v = *reinterpret_cast<const float2*>(sx + 2 * idx);
+      return {v.x, kIn == 1 ? v.y : 0.f};
+    }
+  }
+  // x of a compartment in global memory (a parent's distal compartment)
+  __device__ static float2 gx(const Args& A, long long g) {
+    if (kIn == 1) return static_cast<const float2*>(A.x)[g];
+    return make_float2(static_cast<const float*>(A.x)[g], 0.f);
+  }
+  // acc -= t, accumulating the rounding errors of the leading parts exactly
+  // (two-sum) and everything else in the second word
+  __device__ static void acc_sub(V& s, V& e, const FFV<V>& t) {
+    const V s1 = vsub(s, t.h);
+    const V bb = vsub(s1, s);
+    const V err = vsub(vsub(s, vsub(s1, bb)), vadd(t.h, bb));
+    e = vadd(e, vsub(err, t.l));
+    s = s1;
+  }
+
+  __device__ static void compute(const DevPlan& Pl, const Args& A, int visit, int c0, int n, int lane,
+                                 const Meta<P>& m, unsigned char* buf, const Prev& pv, unsigned char* cache, int cur) {
+    float* sd = reinterpret_cast<float*>(buf);
+    float* su = sd + G::kSlots;
+    float* sb = su + G::kSlots;
+    float* sf = sb + G::kSlots;
+    float* sx = sf + G::kSlots;
+    float4* cslot = reinterpret_cast<float4*>(cache + kCslot);  // [2][kChunk] (u x up, eliminated residual up)
+    float* cx = reinterpret_cast<float*>(cache + kCx);          // [2][kChunk] distal corrections
+    float4* slot = static_cast<float4*>(Pl.cd);
+    float2* xlast = static_cast<float2*>(Pl.xlast);
+    const int L = m.L;
+    if (L == 0) return;
+    const int me = P * lane;
+    const int delta = P == 2 ? L - m.p[P - 1].len : 0;
+    // a cell's root has no parent: its coupling is not part of the system
+#pragma unroll
+    for (int h = 0; h < P; ++h)
+      if (m.p[h].len > 0 && m.p[h].pcomp < 0) su[nidx<P>(L - 1, me + h)] = 0.f;
+    if (visit == 0) {
+      // per piece: the parent's x, and the children's u x and eliminated residuals
+      float xph[P], xpl[P], crh[P], crl[P], ce[P];
+#pragma unroll
+      for (int h = 0; h < P; ++h) {
+        const Piece& q = m.p[h];
+        xph[h] = xpl[h] = crh[h] = crl[h] = ce[h] = 0.f;
+        if (q.len == 0) continue;
+        if (q.pcomp >= 0) {
+          const float2 t = gx(A, q.pcomp);
+          xph[h] = t.x;
+          xpl[h] = t.y;
+        }
+        ff acc = {0.f, 0.f};
+        for (int c = 0; c < q.nchild; ++c) {
+          const int cp = child_pos(Pl, q, c);
+          const int loc = cp - pv.c0;
+          const float4 v = (loc >= 0 && loc < pv.n) ? cslot[pv.which * G::kChunk + loc] : slot_load(slot + cp, q);
+          acc = ff_sub(acc, -v.x, -v.y);
+          ce[h] += v.z;
+        }
+        crh[h] = acc.h;
+        crl[h] = acc.l;
+      }
+      FFV<V> tc{vpack<P>(crh), vpack<P>(crl)};  // the children's u x (at a distal row), or the chain child's
+      V cev = vpack<P>(ce);                    // the children's eliminated residuals times their multipliers
+      FFV<V> un{}, en{};                       // the proximal row's u x and eliminated residual times multiplier
+#pragma unroll
+      for (int r = 0; r < kL; ++r) {
+        if (r < L) {
+          if constexpr (P == 2) {
+            if (r > 0 && r == delta) {
+              tc = {vset_hi(tc.h, crh[1]), vset_hi(tc.l, crl[1])};
+              cev = vset_hi(cev, ce[1]);
+            }
+          }
+          const int i = nidx<P>(r, me);
+          const V dk = ldv(sd, i, V{}), uk = ldv(su, i, V{}), bk = ldv(sb, i, V{}), fk = ldv(sf, i, V{});
+          const FFV<V> xk = ldx(sx, i);
+          FFV<V> xn;
+          if (r < L - 1)
+            xn = ldx(sx, nidx<P>(r + 1, me));
+          else
+            xn = {vpack<P>(xph), vpack<P>(xpl)};
+          V s = bk, e = vsplat(0.f, V{});
+          acc_sub(s, e, vmul_f(xk, dk));
+          acc_sub(s, e, vmul_f(xn, uk));
+          acc_sub(s, e, tc);
+          const V rp = vsub(vadd(s, e), cev);  // the residual, less the children's eliminated residuals
+          stv(sb, i, rp);
+          tc = vmul_f(xk, uk);                 // this row's u x, for the next row (or the parent)
+          cev = vmul(vmul(uk, fk), rp);        // multiplier u / pivot times the eliminated residual
+          un = tc;
+          en = {cev, vsplat(0.f, V{})};
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < P; ++h) {
+        if (m.p[h].len == 0) continue;
+        const float4 out = m.p[h].pcomp >= 0 ? make_float4(vget(un.h, h), vget(un.l, h), vget(en.h, h), 0.f)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        slot[c0 + me + h] = out;
+        cslot[cur * G::kChunk + me + h] = out;
+      }
+      return;
+    }
+    // the correction from the proximal row down, and x + c
+    float cph[P];
+#pragma unroll
+    for (int h = 0; h < P; ++h) {
+      const Piece& q = m.p[h];
+      cph[h] = 0.f;
+      if (q.len > 0 && q.pcomp >= 0) {
+        const int loc = q.ppos - pv.c0;
+        cph[h] = (loc >= 0 && loc < pv.n) ? cx[pv.which * G::kChunk + loc] : xlast[q.ppos].x;
+      }
+    }
+    V cp = vpack<P>(cph);
+    float cm[P], cb = 0.f;
+#pragma unroll
+    for (int h = 0; h < P; ++h) cm[h] = 0.f;
+#pragma unroll
+    for (int r = kL - 1; r >= 0; --r) {
+      if (r < L) {
+        const int i = nidx<P>(r, me);
+        const V uk = ldv(su, i, V{}), rk = ldv(sb, i, V{}), fk = ldv(sf, i, V{});
+        const V c = vmul(vfma(vneg(uk), cp, rk), fk);
+        const FFV<V> xk = ldx(sx, i);
+        // x + c: two-sum of the leading parts, the rest into the low word
+        const V s = vadd(xk.h, c);
+        const V bb = vsub(s, xk.h);
+        const V err = vadd(vsub(xk.h, vsub(s, bb)), vsub(c, bb));
+        const FFV<V> xn = vrenorm(s, vadd(err, xk.l));
+#pragma unroll
+        for (int h = 0; h < P; ++h) {
+          const int q = i + h;
+          if (r >= L - m.p[h].len) cm[h] = fmaxf(cm[h], fabsf(vget(c, h)));
+          if (kOut == 1)
+            reinterpret_cast<double*>(sx)[q] = ff_to_double(vget(xn.h, h), vget(xn.l, h));
+          else
+            reinterpret_cast<float2*>(sx)[q] = make_float2(vget(xn.h, h), vget(xn.l, h));
+        }
+        if constexpr (P == 2) {
+          if (r == delta) cb = f2_hi(c);
+        }
+        cp = c;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < P; ++h) {
+      if (m.p[h].len == 0) continue;
+      const float cd = h == 0 ? vget(cp, 0) : cb;
+      const int pos = c0 + me + h;
+      xlast[pos] = make_float2(cd, 0.f);
+      cx[cur * G::kChunk + me + h] = cd;
+      if (A.bcorr) A.bcorr[Pl.pos_branch[pos]] = cm[h];
+    }
+  }
+
+  __device__ static void copy_out(const DevPlan&, const Args& A, int visit, const Meta<P>& m, int n, int lane,
+                                  unsigned char* buf) {
+    const float* sd = reinterpret_cast<const float*>(buf);
+    const float* sb = sd + 2 * G::kSlots;
+    const float* sx = sd + 4 * G::kSlots;
+    for_chunk_elements(m, n, lane, [&](int i, int, int row, long long g, bool) {
+      const int q = nidx<P>(row, i);
+      if (visit == 0)
+        A.rw[g] = sb[q];
+      else if (kOut == 1)
+        static_cast<double*>(A.xo)[g] = reinterpret_cast<const double*>(sx)[q];
+      else
+        static_cast<float2*>(A.xo)[g] = reinterpret_cast<const float2*>(sx)[q];
+    });
+  }
+};
+
+// ============================================================================
+// Task driver
+// ============================================================================
+// Position in a task's chunk sequence: chunks deepest-first for the
+// elimination (visit 0), root-side first for the substitution (visit 1); a
+// level of more than one chunk's pieces is several chunks.
+struct Pos {
+  int visit, l, c0, n;  // visit == ve: past the end
+};
+
+template <int W>
+__device__ __forceinline__ Pos pos_level(int visit, int l, const int32_t* lp) {
+  const int c0 = __ldg(lp + l), e = __ldg(lp + l + 1) - c0;
+  return {visit, l, c0, e < W ? e : W};
+}
+
+template <int W>
+__device__ __forceinline__ Pos pos_next(Pos p, const int32_t* lp, int nl, int ve) {
+  const int end = __ldg(lp + p.l + 1);
+  if (p.c0 + W < end) {
+    p.c0 += W;
+    p.n = end - p.c0 < W ? end - p.c0 : W;
+    return p;
+  }
+  if (p.visit == 0) {
+    if (p.l > 0) return pos_level<W>(0, p.l - 1, lp);
+    if (ve == 1) return {ve, 0, 0, 0};
+    return pos_level<W>(1, 0, lp);
+  }
+  if (p.l + 1 < nl) return pos_level<W>(1, p.l + 1, lp);
+  return {ve, 0, 0, 0};
+}
+
+template <class M>
+__device__ void run_task(const DevPlan& Pl, const typename M::Args& A, int t, int code, int lane,
+                         unsigned char* wbase) {
+  constexpr int P = M::kPer, W = 32 * P;
+  const int nl = Pl.task_nlvl[t];
+  const int32_t* lp = Pl.tlvl_ptr + Pl.task_lvl_off[t];
+  const int vb = code == 2 ? 1 : 0, ve = code == 1 ? 1 : 2;
+  unsigned char* cache = wbase + M::kStages * M::kStageBytes;
+  auto buf = [wbase](int which) { return wbase + (M::kStages == 2 ? which : 0) * M::kStageBytes; };
+  auto meta = [&](const Pos& p) {
+    return load_meta<M::kPacked, P>(Pl, p.c0, p.n, lane, p.visit < ve, M::kWantDs && p.visit == 1);
+  };
+  // metadata runs two chunks ahead; with two staging buffers the next chunk
+  // is staged while this one is computed, with one right after this one's
+  // results are out
+  Pos cur = pos_level<W>(vb, vb == 0 ? nl - 1 : 0, lp);
+  Meta<P> m_cur = meta(cur);
+  M::stage(Pl, A, cur.visit, m_cur, cur.n, lane, buf(0));
+  Pos nxt = pos_next<W>(cur, lp, nl, ve);
+  Meta<P> m_nxt = meta(nxt);
+  Prev pv{0, 0, 0};  // last chunk of the previous level in this sweep
+  int which = 0;
+  while (cur.visit < ve) {
+    cp_wait_all();
+    __syncwarp();
+    // nothing of the substitution is read before the elimination has
+    // finished: its first chunks reuse positions the elimination is still
+    // writing (and read the folded states it leaves)
+    const bool crossing = nxt.visit != cur.visit;
+    if (M::kStages == 2 && nxt.visit < ve && !crossing)
+      M::stage(Pl, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1));
+    const Pos nn = nxt.visit < ve ? pos_next<W>(nxt, lp, nl, ve) : nxt;
+    Meta<P> m_nn = meta(nn);
+    M::compute(Pl, A, cur.visit, cur.c0, cur.n, lane, m_cur, buf(which), pv, cache, cur.l & 1);
+    __syncwarp();
+    M::copy_out(Pl, A, cur.visit, m_cur, cur.n, lane, buf(which));
+    __syncwarp();
+    if (crossing && nxt.visit < ve) {
+      m_nxt = meta(nxt);
+      m_nn = meta(nn);
+    }
+    if (nxt.visit < ve && (crossing || M::kStages == 1))
+      M::stage(Pl, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1));
+    // predecessor of the next chunk: the last chunk of the level before its level, same sweep
+    if (crossing) {
+      pv = Prev{0, 0, 0};
+    } else if (nxt.l != cur.l) {
+      pv = Prev{cur.c0, cur.n, cur.l & 1};
+    }
+    cur = nxt;
+    m_cur = m_nxt;
+    nxt = nn;
+    m_nxt = m_nn;
+    which ^= 1;
+  }
+}
+
+// After a subtree task's elimination: count its units off their cell's
+// pending count; the warp that finishes the cell's last subtree takes over
+// the cell's top part (both visits) as its next task.  Nothing waits: the
+// hand-over goes to whoever arrives last.  Release: every lane fences its slot
+// writes before lane 0's atomic; acquire: the fence after it, and the top
+// part reads those slots through L2.  Returns the top task, or -1.
+__device__ __forceinline__ int hand_over(const DevPlan& P, int t, int lane) {
+  __threadfence();
+  __syncwarp();
+  const int cell = __ldg(P.task_sub + 2 * t);
+  if (cell < 0) return -1;
+  int last = 0;
+  if (lane == 0) {
+    const int cnt = __ldg(P.task_sub + 2 * t + 1);
+    last = atomicSub(P.cell_pending + cell, cnt) == cnt;
+  }
+  if (!__shfl_sync(kFull, last, 0)) return -1;
+  __threadfence();
+  return __ldg(P.cell_top_task + cell);
+}
+
+template <class M>
+__global__ void __launch_bounds__(32 * kWarps, M::kMinBlocks) k_units(DevPlan P, typename M::Args A, int phase) {
+  extern __shared__ __align__(16) unsigned char smem_u[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* wbase = smem_u + w * M::kWarpBytes;
+  const int e0 = P.phase_off[phase], ne = P.phase_off[phase + 1] - e0;
+  int next = -1;  // a top part handed over to this warp
+  for (;;) {
+    int t, code;
+    if (next >= 0) {
+      t = next;
+      code = 0;
+      next = -1;
+    } else {
+      int k = 0;
+      if (lane == 0) k = atomicAdd(P.counter + phase, 1);
+      k = __shfl_sync(kFull, k, 0);
+      if (k >= ne) break;
+      const int e = P.phase_entry[e0 + k];
+      t = e >> 2;
+      code = e & 3;
+    }
+    run_task<M>(P, A, t, code, lane, wbase);
+    if (code == 1) next = hand_over(P, t, lane);
+  }
+}
+
+template <class M>
+cudaError_t grid_of(const DevPlan& P, int* grid) {
+  int per_sm = 0;
+  const size_t smem = (size_t)kWarps * M::kWarpBytes;
+  cudaError_t e = cudaFuncSetAttribute(k_units<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_units<M>, 32 * kWarps, smem);
+  if (e != cudaSuccess) return e;
+  *grid = P.sms * (per_sm > 0 ? per_sm : 1);
+  return cudaSuccess;
+}
+
+template <class M>
+cudaError_t launch_phases(const DevPlan& P, const typename M::Args& A, int grid, cudaStream_t s) {
+  if (P.n_wtasks == 0) return cudaSuccess;
+  const size_t smem = (size_t)kWarps * M::kWarpBytes;
+  // work counters to 0 and per-cell subtree counts to their full values
+  cudaError_t e = cudaMemcpyAsync(P.counter, P.counter_init, (4 + (size_t)P.n_cells) * sizeof(int32_t),
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  for (int phase = 0; phase < 3; ++phase) {
+    const int ne = P.phase_off[phase + 1] - P.phase_off[phase];
+    if (ne == 0) continue;
+    const int warps = ne < grid * kWarps ? ne : grid * kWarps;
+    const int blocks = (warps + kWarps - 1) / kWarps;
+    k_units<M><<<blocks, 32 * kWarps, smem, s>>>(P, A, phase);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ---- the modes' instantiations for P pieces per lane --------------------------
+template <int PL>
+struct UnitKernels {
+  using F64 = FactorMode<double, false, false, PL>;
+  using F32 = FactorMode<float, false, false, PL>;
+  using Cable = FactorMode<double, true, false, PL>;
+  using Comp = CompMode<false, PL>;
+  using PkF64 = FactorMode<double, false, true, PL>;
+  using PkF32 = FactorMode<float, false, true, PL>;
+  using PkComp = CompMode<true, PL>;
+  using PkCable = FactorMode<double, true, true, PL>;
+  using F32Reuse = FactorMode<float, false, false, PL, true>;
+  using CableReuse = FactorMode<double, true, false, PL, true>;
+  using PkCableReuse = FactorMode<double, true, true, PL, true>;
+  using R32to2 = RefineMode<PL, 0, 0>;
+  using R32to64 = RefineMode<PL, 0, 1>;
+  using R2to2 = RefineMode<PL, 1, 0>;
+  using R2to64 = RefineMode<PL, 1, 1>;
+
+  static cudaError_t prepare(DevPlan& P) {
+    cudaError_t e = grid_of<F64>(P, &P.grid[0]);
+    if (e == cudaSuccess) e = grid_of<F32>(P, &P.grid[1]);
+    if (e == cudaSuccess) e = grid_of<Cable>(P, &P.grid[2]);
+    if (e == cudaSuccess) e = grid_of<Comp>(P, &P.grid[3]);
+    if (e == cudaSuccess) e = grid_of<PkF64>(P, &P.grid[4]);
+    if (e == cudaSuccess) e = grid_of<PkF32>(P, &P.grid[5]);
+    if (e == cudaSuccess) e = grid_of<PkComp>(P, &P.grid[6]);
+    if (e == cudaSuccess) e = grid_of<PkCable>(P, &P.grid[7]);
+    int g_reuse = 0;  // same footprint as the plain modes
+    if (e == cudaSuccess) e = grid_of<F32Reuse>(P, &g_reuse);
+    if (e == cudaSuccess) e = grid_of<CableReuse>(P, &g_reuse);
+    if (e == cudaSuccess) e = grid_of<PkCableReuse>(P, &g_reuse);
+    if (e == cudaSuccess) e = grid_of<R32to2>(P, &P.grid_refine);
+    if (e == cudaSuccess) e = grid_of<R32to64>(P, &g_reuse);
+    if (e == cudaSuccess) e = grid_of<R2to2>(P, &g_reuse);
+    if (e == cudaSuccess) e = grid_of<R2to64>(P, &g_reuse);
+    return e;
+  }
+
+  static cudaError_t run(const DevPlan& P, const UnitCall& c, cudaStream_t s) {
+    const double* d8 = static_cast<const double*>(c.d);
+    const double* u8 = static_cast<const double*>(c.u);
+    const double* s8 = static_cast<const double*>(c.s);
+    const double* g8 = static_cast<const double*>(c.g);
+    double* x8 = static_cast<double*>(c.x);
+    const float* d4 = static_cast<const float*>(c.d);
+    const float* u4 = static_cast<const float*>(c.u);
+    const float* b4 = static_cast<const float*>(c.b);
+    float* x4 = static_cast<float*>(c.x);
+    const double th = (double)c.theta;
+    switch (c.op) {
+      case UnitOp::F64:
+        return launch_phases<F64>(P, {d8, u8, nullptr, nullptr, x8, 0.0, 0.0, 0.0, false}, P.grid[0], s);
+      case UnitOp::F32:
+        return launch_phases<F32>(P, {d4, u4, nullptr, nullptr, x4, 0.f, 0.f, 0.f, false,
+                                      static_cast<const float*>(c.rhs)}, P.grid[1], s);
+      case UnitOp::F32Resolve:
+        return launch_phases<F32Reuse>(P, {nullptr, u4, nullptr, nullptr, x4, 0.f, 0.f, 0.f, false}, P.grid[1], s);
+      case UnitOp::Comp:
+        return launch_phases<Comp>(P, {d4, u4, b4, x8}, P.grid[3], s);
+      case UnitOp::Cable:
+        return launch_phases<Cable>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, c.rhs_from_V}, P.grid[2], s);
+      case UnitOp::CableReuse:
+        return launch_phases<CableReuse>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, true}, P.grid[2], s);
+      case UnitOp::PkF64:
+        return launch_phases<PkF64>(P, {d8, u8, nullptr, nullptr, x8, 0.0, 0.0, 0.0, false}, P.grid[4], s);
+      case UnitOp::PkF32:
+        return launch_phases<PkF32>(P, {d4, u4, nullptr, nullptr, x4, 0.f, 0.f, 0.f, false}, P.grid[5], s);
+      case UnitOp::PkComp:
+        return launch_phases<PkComp>(P, {d4, u4, b4, x8}, P.grid[6], s);
+      case UnitOp::PkCable:
+        return launch_phases<PkCable>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, c.rhs_from_V}, P.grid[7], s);
+      case UnitOp::PkCableReuse:
+        return launch_phases<PkCableReuse>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, true}, P.grid[7], s);
+      case UnitOp::Refine32to2:
+        return launch_phases<R32to2>(P, {d4, u4, b4, c.rhs, c.rw, c.x, c.bcorr}, P.grid_refine, s);
+      case UnitOp::Refine32to64:
+        return launch_phases<R32to64>(P, {d4, u4, b4, c.rhs, c.rw, c.x, c.bcorr}, P.grid_refine, s);
+      case UnitOp::Refine2to2:
+        return launch_phases<R2to2>(P, {d4, u4, b4, c.rhs, c.rw, c.x, c.bcorr}, P.grid_refine, s);
+      case UnitOp::Refine2to64:
+        return launch_phases<R2to64>(P, {d4, u4, b4, c.rhs, c.rw, c.x, c.bcorr}, P.grid_refine, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+};
+
+}  // namespace
+}  // namespace hines

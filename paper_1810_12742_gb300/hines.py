@@ -48,7 +48,7 @@ class HinesError(RuntimeError):
 
 
 class PlanOpts(ctypes.Structure):
-    _fields_ = [("host_only", ctypes.c_int32), ("split_branches", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
+    _fields_ = [("host_only", ctypes.c_int32), ("split_branches", ctypes.c_int32), ("pieces_per_lane", ctypes.c_int32),
                 ("sort_by_length", ctypes.c_int32), ("pack_compartments", ctypes.c_int32),
                 ("reroot", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
@@ -125,14 +125,17 @@ class Plan:
     p[0] = -1, p[i] < i), concatenated.  host_only builds the schedule without
     touching the GPU (for inspection).  reroot re-roots every cell at its
     centre (Section 6); such a plan takes solver-layout arrays only (pack node
-    arrays with ``pack``, couplings with ``pack_coupling``)."""
+    arrays with ``pack``, couplings with ``pack_coupling``).  pieces_per_lane:
+    branch pieces each warp lane owns in a chunk (1, the default, or 2).
+    split_branches: False/0, True/1 (Section 6's split at the batch's level
+    means) or 2 (the same at each cell's own level means)."""
 
-    def __init__(self, ncomp, parent, split_branches: bool = False, host_only: bool = False, cta_threads: int = 0,
+    def __init__(self, ncomp, parent, split_branches: bool = False, host_only: bool = False, pieces_per_lane: int = 0,
                  sort_by_length: bool = False, pack_compartments: int = 0, reroot: bool = False):
         self._h = ctypes.c_void_p()
         nc = np.ascontiguousarray(ncomp, np.int32)
         pa = np.ascontiguousarray(parent, np.int32)
-        opts = PlanOpts(int(host_only), int(split_branches), int(cta_threads), int(sort_by_length),
+        opts = PlanOpts(int(host_only), int(split_branches), int(pieces_per_lane), int(sort_by_length),
                         int(pack_compartments), int(reroot))
         _check(lib().hines_plan_create(ctypes.byref(self._h), nc.size, _np_ptr(nc), _np_ptr(pa), ctypes.byref(opts)),
                "hines_plan_create")
@@ -146,6 +149,7 @@ class Plan:
         self.workspace_bytes = info.workspace_bytes
         self.metadata_bytes = info.metadata_bytes
         self.n_packed = info.n_packed
+        self.pieces_per_lane = int(pieces_per_lane) or 1
         self.host_only = host_only
         self.rerooted = bool(reroot)
         off = np.empty(self.n_cells + 1, np.int64)

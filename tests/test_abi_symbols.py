@@ -48,7 +48,7 @@ def test_argument_errors_without_gpu():
     opts.reserved[0] = 1
     assert L.hines_plan_create(ctypes.byref(h), 1, nc.ctypes.data_as(ctypes.c_void_p),
                                pa.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts)) == H.HINES_ERR_INVALID_ARG
-    opts = H.PlanOpts(1, 0, 48)  # not a multiple of 32
+    opts = H.PlanOpts(1, 0, 3)  # pieces per lane: 1 or 2 only
     assert L.hines_plan_create(ctypes.byref(h), 1, nc.ctypes.data_as(ctypes.c_void_p),
                                pa.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts)) == H.HINES_ERR_INVALID_ARG
     plan = H.Plan(nc, pa, host_only=True)
@@ -64,4 +64,7 @@ def test_argument_errors_without_gpu():
     # but its solver layout can be inspected: 2 compartments in one chunk, padded to 4 slots
     assert plan.n_packed == 4
     assert plan.export_packed().tolist() == [1, 0, -1, -1]
+    # two pieces per lane: each row holds the lane's pair (the second piece absent here)
+    two = H.Plan(nc, pa, host_only=True, pieces_per_lane=2)
+    assert two.export_packed().tolist() == [1, -1, 0, -1]
     assert L.hines_plan_destroy(None) == H.HINES_OK

@@ -65,10 +65,11 @@ def _same(x, xp, mode, off):
 
 
 @pytest.mark.parametrize("mode", ["f64", "f32", "comp"])
-@pytest.mark.parametrize("split", [False, True])
-def test_packed_solves_equal_natural_zoo(mode, split):
+@pytest.mark.parametrize("split", [0, 1, 2])
+@pytest.mark.parametrize("per_lane", [1, 2])
+def test_packed_solves_equal_natural_zoo(mode, split, per_lane):
     ncomp, parent, c = zoo_batch(43)
-    plan = H.Plan(ncomp, parent, split_branches=split)
+    plan = H.Plan(ncomp, parent, split_branches=split, pieces_per_lane=per_lane)
     x, xp = _natural_and_packed(plan, dev(c["d"]), dev(c["u"]), dev(c["b"]), mode)
     _same(x, xp, mode, np.concatenate(([0], np.cumsum(ncomp))))
     widen = mode != "f64"
@@ -80,9 +81,10 @@ def test_packed_solves_equal_natural_zoo(mode, split):
 
 @pytest.mark.parametrize("mode", ["f64", "f32", "comp"])
 @pytest.mark.parametrize("pack", [0, -1])
-def test_packed_solves_equal_natural_uneven(mode, pack):
+@pytest.mark.parametrize("per_lane", [1, 2])
+def test_packed_solves_equal_natural_uneven(mode, pack, per_lane):
     pop = uneven_subset()
-    plan = H.Plan(pop["ncomp"], pop["parent"], pack_compartments=pack)
+    plan = H.Plan(pop["ncomp"], pop["parent"], pack_compartments=pack, pieces_per_lane=per_lane)
     x, xp = _natural_and_packed(plan, dev(pop["d"]), dev(pop["u"]), dev(pop["b"]), mode)
     _same(x, xp, mode, pop["offsets"])
 
@@ -116,12 +118,15 @@ def test_packed_misaligned_rejected():
 
 def test_host_pipeline_equals_device_solve():
     """The overlapped host-array pipeline (pieces with their own plans) gives
-    the whole-batch compensated solve bit for bit: cells are independent and
-    each branch's arithmetic does not depend on how cells are grouped."""
+    the whole-batch compensated solve to rounding: cells are independent, but
+    each piece's plan cuts long branches at multiples of 8 of its own buffers,
+    so the pieces' chains (and their roundings) can differ from the whole
+    batch's.  Both stay within the FP32-input gate of the oracle."""
     pop = uneven_subset()
     plan = H.Plan(pop["ncomp"], pop["parent"])
     f32 = {k: pop[k].astype(np.float32) for k in ("d", "u", "b")}
-    x = H.solve_compensated(plan, *(dev(f32[k], torch.float32) for k in ("d", "u", "b")))
+    x = H.solve_compensated(plan, *(dev(f32[k], torch.float32) for k in ("d", "u", "b"))).cpu().numpy()
+    ref = oracle.solve_batch(pop["ncomp"], pop["parent"], *(f32[k].astype(np.float64) for k in ("d", "u", "b")))
     host = {k: torch.as_tensor(f32[k]).pin_memory() for k in ("d", "u", "b")}
     xh = torch.empty(plan.n_unknowns, dtype=torch.float64).pin_memory()
     for pieces in (1, 3, 7):
@@ -129,4 +134,8 @@ def test_host_pipeline_equals_device_solve():
         xh.zero_()
         pipe.solve_compensated(host["d"], host["u"], host["b"], xh)
         torch.cuda.synchronize()
-        assert torch.equal(xh, x.cpu())
+        got = xh.numpy()
+        if pieces == 1:
+            assert np.array_equal(got, x)  # one piece: the same plan, the same arithmetic
+        assert cell_rel_err(got, x, plan.offsets).max() <= 1e-12
+        assert cell_rel_err(got, ref, plan.offsets).max() <= 1e-10

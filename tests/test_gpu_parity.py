@@ -50,11 +50,11 @@ def zoo_batch(seed, sizes=(1, 2, 3, 17, 64, 65, 300, 1000)):
     return ncomp, np.concatenate(trees), {k: np.concatenate(v) for k, v in coef.items()}
 
 
-@pytest.mark.parametrize("split", [False, True])
-@pytest.mark.parametrize("cta", [0, 64, 1024])
-def test_solve_f64_zoo(split, cta):
+@pytest.mark.parametrize("split", [0, 1, 2])
+@pytest.mark.parametrize("per_lane", [1, 2])
+def test_solve_f64_zoo(split, per_lane):
     ncomp, parent, c = zoo_batch(31)
-    plan = H.Plan(ncomp, parent, split_branches=split, cta_threads=cta)
+    plan = H.Plan(ncomp, parent, split_branches=split, pieces_per_lane=per_lane)
     x = dev(c["b"])
     H.solve(plan, dev(c["d"]), dev(c["u"]), x)
     ref = oracle.solve_batch(ncomp, parent, c["d"], c["u"], c["b"])
@@ -112,13 +112,14 @@ def test_solve_f32(name):
 
 
 @pytest.mark.parametrize("steps", [1, 2])
-def test_solve_refine_mixed_population(steps):
+@pytest.mark.parametrize("per_lane", [1, 2])
+def test_solve_refine_mixed_population(steps, per_lane):
     w = I.WORKLOADS["uneven_mixed"]
     cls = I.cell_classes(w)
     cells = np.concatenate([np.nonzero(cls == 0)[0][:24], np.nonzero(cls == 1)[0][:3]])
     pop = I.population(w, cells=cells, margin=1e-1)
     f = _widened(pop)
-    plan = H.Plan(pop["ncomp"], pop["parent"])
+    plan = H.Plan(pop["ncomp"], pop["parent"], pieces_per_lane=per_lane)
     relres = torch.empty(plan.n_cells, dtype=torch.float64, device="cuda")
     x = H.solve_refine(plan, *(dev(f[k], torch.float32) for k in ("d", "u", "b")), steps=steps, relres=relres)
     ref = oracle.solve_batch(pop["ncomp"], pop["parent"], *(f[k].astype(np.float64) for k in ("d", "u", "b")))
@@ -131,22 +132,24 @@ def test_solve_refine_mixed_population(steps):
     assert plan.status() in (0, H.HINES_WARN_REFINE)
 
 
-def test_solve_refine_zoo_edge_cases():
+@pytest.mark.parametrize("per_lane", [1, 2])
+def test_solve_refine_zoo_edge_cases(per_lane):
     ncomp, parent, c = zoo_batch(33)
     f = {k: c[k].astype(np.float32) for k in ("d", "u", "b")}
-    plan = H.Plan(ncomp, parent)
+    plan = H.Plan(ncomp, parent, pieces_per_lane=per_lane)
     x = H.solve_refine(plan, *(dev(f[k], torch.float32) for k in ("d", "u", "b")), steps=2)
     ref = oracle.solve_batch(ncomp, parent, *(f[k].astype(np.float64) for k in ("d", "u", "b")))
     assert cell_rel_err(x.cpu().numpy(), ref, plan.offsets).max() <= TOL_REFINE
 
 
 @pytest.mark.parametrize("theta", [0, 1])
-def test_cable_steps_match_oracle(theta):
+@pytest.mark.parametrize("per_lane", [1, 2])
+def test_cable_steps_match_oracle(theta, per_lane):
     w = I.WORKLOADS["uneven_steps"]
     cls = I.cell_classes(w)
     cells = np.concatenate([np.nonzero(cls == 0)[0][:12], np.nonzero(cls == 1)[0][:2]])
     pop = I.population(w, cells=cells, keys=("s", "a", "u", "g", "V0"))
-    plan = H.Plan(pop["ncomp"], pop["parent"])
+    plan = H.Plan(pop["ncomp"], pop["parent"], pieces_per_lane=per_lane)
     s, g, u = dev(pop["s"]), dev(pop["g"]), dev(pop["u"])
     V = dev(pop["V0"])
     K = 15
@@ -192,11 +195,12 @@ def test_wrong_device_arguments_rejected():
         H.solve(plan, dev(np.zeros(4)), dev(np.zeros(4)), dev(np.zeros(4)))
 
 
-def test_solve_compensated_zoo_edge_cases():
+@pytest.mark.parametrize("per_lane", [1, 2])
+def test_solve_compensated_zoo_edge_cases(per_lane):
     ncomp, parent, c = zoo_batch(35)
     f = {k: c[k].astype(np.float32) for k in ("d", "u", "b")}
-    for split in (False, True):
-        plan = H.Plan(ncomp, parent, split_branches=split)
+    for split in (0, 1, 2):
+        plan = H.Plan(ncomp, parent, split_branches=split, pieces_per_lane=per_lane)
         x = H.solve_compensated(plan, *(dev(f[k], torch.float32) for k in ("d", "u", "b")))
         ref = oracle.solve_batch(ncomp, parent, *(f[k].astype(np.float64) for k in ("d", "u", "b")))
         assert cell_rel_err(x.cpu().numpy(), ref, plan.offsets).max() <= TOL_REFINE
@@ -221,6 +225,22 @@ def test_solve_compensated_margin_sweep(margin):
     f = _widened(pop)
     plan = H.Plan(pop["ncomp"], pop["parent"])
     x = H.solve_compensated(plan, *(dev(f[k], torch.float32) for k in ("d", "u", "b")))
+    ref = oracle.solve_batch(pop["ncomp"], pop["parent"], *(f[k].astype(np.float64) for k in ("d", "u", "b")))
+    assert cell_rel_err(x.cpu().numpy(), ref, plan.offsets).max() <= TOL_REFINE
+
+
+@pytest.mark.parametrize("margin,steps", [(1e-1, 1), (1e-1, 2), (1e-3, 2)])
+def test_solve_refine_margin_sweep(margin, steps):
+    """FP32 elimination with refinement steps against the oracle at the
+    leak margins where the refinement reaches the 1e-10 gate (one step at
+    margin 0.1, two at 1e-3)."""
+    w = I.WORKLOADS["uneven_mixed"]
+    cls = I.cell_classes(w)
+    cells = np.concatenate([np.nonzero(cls == 0)[0][:24], np.nonzero(cls == 1)[0][:3]])
+    pop = I.population(w, cells=cells, margin=margin)
+    f = _widened(pop)
+    plan = H.Plan(pop["ncomp"], pop["parent"])
+    x = H.solve_refine(plan, *(dev(f[k], torch.float32) for k in ("d", "u", "b")), steps=steps)
     ref = oracle.solve_batch(pop["ncomp"], pop["parent"], *(f[k].astype(np.float64) for k in ("d", "u", "b")))
     assert cell_rel_err(x.cpu().numpy(), ref, plan.offsets).max() <= TOL_REFINE
 

@@ -28,17 +28,25 @@ def py_branches(p):
     return br
 
 
-def py_split(cells):
-    """Section 6 splitting: per level over the whole batch, cut branches longer
-    than the level mean (strictly) after ceil(len/2) compartments."""
+def py_split(cells, local=False):
+    """Section 6 splitting: per level, cut branches longer than the level mean
+    (strictly) after ceil(len/2) compartments; the mean over the whole batch,
+    or (local) over each cell's own branches on the level."""
     level = 0
     while True:
         lens = [b[1] for bs in cells for b in bs if b[3] == level]
         if not lens:
             return cells
-        mean = float(np.sum(np.array(lens, np.float64))) / len(lens)
+        global_mean = float(np.sum(np.array(lens, np.float64))) / len(lens)
         new_cells = []
         for bs in cells:
+            mean = global_mean
+            if local:
+                own = [b[1] for b in bs if b[3] == level]
+                if not own:
+                    new_cells.append(bs)
+                    continue
+                mean = float(np.sum(np.array(own, np.float64))) / len(own)
             out, prox, dist = [], {}, {}
             for j, b in enumerate(bs):
                 prox[j] = len(out)
@@ -62,23 +70,26 @@ def py_split(cells):
         level += 1
 
 
-CAP, LANES = 16, 32
+CAP, LANES, ALIGN = 16, 32, 8
 
 
-def py_cap(bs, cap=CAP):
-    """Branches longer than cap become ceil(len/cap) chained pieces; the first
-    len % pieces pieces (from the proximal end) are one longer."""
+def py_cap(bs, base, cap=CAP):
+    """Branches longer than cap become chained pieces: from the proximal end,
+    each piece reaches the farthest multiple of ALIGN (global natural index,
+    the cell starting at `base`) within cap compartments, or the branch end."""
     out, last = [], {}
     for j, b in enumerate(bs):
-        pieces = -(-b[1] // cap)
-        base, rem = divmod(b[1], pieces)
         parent = -1 if b[2] < 0 else last[b[2]]
-        first = b[0]
-        for k in range(pieces):
-            ln = base + (1 if k < rem else 0)
-            out.append([first, ln, parent, 0 if parent < 0 else out[parent][3] + 1])
+        start, end = b[0], b[0] + b[1]
+        while start < end:
+            stop = min(end, start + cap)
+            if stop < end:
+                down = stop - (base + stop) % ALIGN
+                if down > start:
+                    stop = down
+            out.append([start, stop - start, parent, 0 if parent < 0 else out[parent][3] + 1])
             parent = len(out) - 1
-            first += ln
+            start = stop
         last[j] = parent
     return out
 
@@ -121,7 +132,7 @@ def py_units(ncomp, cells_flat):
     return units
 
 
-def py_tasks(ncomp, units, sort_by_length, pack=24576):
+def py_tasks(ncomp, units, sort_by_length, pack=24576, width=32):
     rl = {}
     for kind, c, root, ids in units:
         for b in ids:
@@ -139,8 +150,8 @@ def py_tasks(ncomp, units, sort_by_length, pack=24576):
             usize = sum(G["len"][b] for b in u[3])
             if kind == 2 or (kind == 1 and groups and groups[-1][0][1] != u[1]):
                 fits = False  # a top part alone; subtrees of one cell per task
-            elif pack < 0:  # Section 4's rule: every level at most 32 branches
-                fits = bool(groups) and all((cnt[l] if l < len(cnt) else 0) + cc[l] <= LANES for l in range(len(cc)))
+            elif pack < 0:  # Section 4's rule: every level at most a chunk's width of branches
+                fits = bool(groups) and all((cnt[l] if l < len(cnt) else 0) + cc[l] <= width for l in range(len(cc)))
             else:
                 fits = bool(groups) and gsize + usize <= pack
             if not fits:
@@ -152,14 +163,15 @@ def py_tasks(ncomp, units, sort_by_length, pack=24576):
             cnt = [(cnt[l] if l < len(cnt) else 0) + (cc[l] if l < len(cc) else 0) for l in range(max(len(cnt), len(cc)))]
         for g in groups:
             ids = [b for u in g for b in u[3]]
-            tasks.append((kind, py_hu(ids, rl, sort_by_length)))
+            tasks.append((kind, py_hu(ids, rl, sort_by_length, width)))
     return tasks
 
 
-def py_hu(ids, rl, sort_by_length):
-    """Hu's list schedule of a task's dependency forest: chunks of at most 32
-    ready branches (all children in the task in earlier chunks), farthest from
-    the unit root first; positions list the chunks root-side first."""
+def py_hu(ids, rl, sort_by_length, width):
+    """Hu's list schedule of a task's dependency forest: chunks of at most
+    `width` ready branches (all children in the task in earlier chunks),
+    farthest from the unit root first; each chunk then ordered by length,
+    longest first (stable); positions list the chunks root-side first."""
     inset = set(ids)
     pend = dict.fromkeys(ids, 0)
     for b in ids:
@@ -173,14 +185,15 @@ def py_hu(ids, rl, sort_by_length):
     heapq.heapify(heap)
     chunks = []
     while heap:
-        ch = [heapq.heappop(heap)[-1] for _ in range(min(LANES, len(heap)))]
-        chunks.append(ch)
+        ch = [heapq.heappop(heap)[-1] for _ in range(min(width, len(heap)))]
         for b in ch:
             p = G["parent"][b]
             if p in inset:
                 pend[p] -= 1
                 if pend[p] == 0:
                     heapq.heappush(heap, key(p))
+        ch.sort(key=lambda b: -G["len"][b])  # stable
+        chunks.append(ch)
     G.setdefault("chunks", []).extend(list(reversed(chunks)))
     return [b for ch in reversed(chunks) for b in ch]
 
@@ -188,12 +201,12 @@ def py_hu(ids, rl, sort_by_length):
 G = {}
 
 
-def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0):
+def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0, per_lane=1):
     off = np.concatenate(([0], np.cumsum(ncomp))).astype(np.int64)
     cells = [py_branches(parent[off[c]:off[c + 1]]) for c in range(len(ncomp))]
     if split:
-        cells = py_split(cells)
-    cells = [py_cap(bs) for bs in cells]
+        cells = py_split(cells, local=split == 2)
+    cells = [py_cap(bs, int(off[c])) for c, bs in enumerate(cells)]
     first, length, pbr, level, cell, order = [], [], [], [], [], []
     base = 0
     for c, bs in enumerate(cells):
@@ -216,7 +229,7 @@ def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0):
     units = py_units(list(ncomp), cells_flat)
     if pack == 0:  # default: 24576, smaller so that a small batch gives 2048 tasks where units allow
         pack = min(24576, max(1, -(-int(np.sum(ncomp)) // 2048)))
-    tasks = py_tasks(list(ncomp), units, sort_by_length, pack)
+    tasks = py_tasks(list(ncomp), units, sort_by_length, pack, LANES * per_lane)
     nb = len(first)
     branch_task = np.full(nb, -1, np.int64)
     branch_kind = np.zeros(nb, np.int64)
@@ -233,12 +246,12 @@ def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0):
     return out
 
 
-def _compare(ncomp, parent, split, sort_by_length=False, pack=0):
+def _compare(ncomp, parent, split, sort_by_length=False, pack=0, per_lane=1):
     plan = H.Plan(ncomp, parent, split_branches=split, host_only=True, sort_by_length=sort_by_length,
-                  pack_compartments=pack)
+                  pack_compartments=pack, pieces_per_lane=per_lane)
     got = plan.export()
     got.update(plan.export_tasks())
-    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split, sort_by_length, pack)
+    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split, sort_by_length, pack, per_lane)
     assert plan.n_tasks == ref.pop("n_tasks")
     for k in ref:
         assert np.array_equal(got[k], ref[k]), k
@@ -246,23 +259,36 @@ def _compare(ncomp, parent, split, sort_by_length=False, pack=0):
     assert plan.n_unknowns == int(np.sum(ncomp))
     slots = plan.export_packed()
     assert plan.n_packed == slots.size
-    assert np.array_equal(slots, py_packed(got))
+    assert np.array_equal(slots, py_packed(got, per_lane))
     return got
 
 
-def py_packed(ex):
+def py_packed(ex, per_lane):
     """Restatement of the solver layout: one block per chunk of the schedule
-    (chunks in position order); in a chunk's block, row r lists the r-th
-    compartment from the distal end of every branch longer than r, in lane
-    order; blocks padded to multiples of 4 slots."""
+    (chunks in position order).  Lane j of a chunk owns its branches
+    per_lane*j .. per_lane*j + per_lane - 1 and spans as many rows as its first
+    (longest) branch has compartments; the lane's branches are aligned at their
+    proximal ends.  Row r lists, for every lane spanning more than r rows, one
+    slot per owned branch: the compartment r rows from the lane's distal start
+    (r-th from the distal end of the longest; the same distance from the
+    proximal end for the other), or padding (-1).  Blocks padded to multiples
+    of 4 slots."""
     ln, first = ex["len"], ex["first"]
     slots = []
     for chunk in G["chunks"]:
+        lanes = [chunk[k:k + per_lane] for k in range(0, len(chunk), per_lane)]
         e = 0
         for r in range(CAP):
-            for b in chunk:
-                if ln[b] > r:
-                    slots.append(first[b] + ln[b] - 1 - r)
+            for own in lanes:
+                rows = ln[own[0]]
+                if rows <= r:
+                    continue
+                for h in range(per_lane):
+                    t = rows - 1 - r  # distance from the proximal end
+                    if h < len(own) and t < ln[own[h]]:
+                        slots.append(first[own[h]] + t)
+                    else:
+                        slots.append(-1)
                     e += 1
         slots += [-1] * (-e % 4)
     return np.array(slots, np.int64)
@@ -280,20 +306,21 @@ def test_solver_layout_is_a_permutation():
     assert plan.n_packed % 4 == 0
 
 
-@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("split", [0, 1, 2])
 @pytest.mark.parametrize("sort_by_length", [False, True])
 @pytest.mark.parametrize("pack", [0, -1, 700])
-def test_zoo_matches_restatement(split, sort_by_length, pack):
+@pytest.mark.parametrize("per_lane", [1, 2])
+def test_zoo_matches_restatement(split, sort_by_length, pack, per_lane):
     rng = np.random.default_rng(21)
     trees = []
     for n in (1, 2, 5, 33, 250, 5000):
         trees += list(tree_zoo(rng, n).values())
     ncomp = [t.size for t in trees]
-    _compare(ncomp, np.concatenate(trees), split, sort_by_length, pack)
+    _compare(ncomp, np.concatenate(trees), split, sort_by_length, pack, per_lane)
 
 
 @pytest.mark.parametrize("name", ["fp64_small", "fp64_uniform", "uneven_steps", "adjoint"])
-@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("split", [0, 1, 2])
 def test_workload_samples_match_restatement(name, split):
     w = I.WORKLOADS[name]
     cells = np.arange(min(w.n_cells, 24))
@@ -342,7 +369,8 @@ def test_split_shortens_long_branches():
     a = H.Plan(ncomp, parent, split_branches=False, host_only=True)
     b = H.Plan(ncomp, parent, split_branches=True, host_only=True)
     ea, eb = a.export(), b.export()
-    assert b.n_branches > a.n_branches
+    # (the piece count can go either way: the cap cuts at aligned indices,
+    # and a midpoint split can leave fewer aligned pieces than it adds)
     assert eb["len"].max() <= ea["len"].max()
     assert b.max_levels > a.max_levels
 
