@@ -87,7 +87,11 @@ typedef struct {
                               HINES_ERR_INVALID_ARG, and hines_pack / hines_pack_coupling /
                               hines_unpack map straight between the caller's numbering
                               and its solver layout */
-  int32_t reserved[2];     /* must be zero */
+  int32_t even_cuts;       /* 0: branches longer than 16 are cut from the proximal end at the
+                              farthest multiple of 8 (natural layout) within 16 compartments, so
+                              that pieces share no 32-byte sector; 1: into ceil(len / 16) pieces
+                              of near-equal length, wherever their boundaries fall */
+  int32_t reserved[1];     /* must be zero */
 } hines_plan_opts;
 
 /* Plan summary. */
@@ -115,7 +119,7 @@ typedef struct {
  * (maximal unbranched runs: compartment i starts a branch when i = 0,
  * p[i] != i-1, or p[i] has two or more children), optionally splits branches
  * longer than their level's mean (Section 6), cuts every branch longer than
- * 16 compartments into near-equal chained pieces, assigns levels (number of
+ * 16 compartments into chained pieces (see even_cuts), assigns levels (number of
  * ancestor branches), cuts cells of more than 4096 compartments into a top
  * part and subtrees, packs these units into warp tasks (by size, or by
  * Section 4's greedy rule with the lanes of a warp), cuts every task into

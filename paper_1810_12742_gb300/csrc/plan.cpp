@@ -131,7 +131,10 @@ bool split_level(std::vector<std::vector<Br>>& cells, int32_t level, bool local)
 // sector of an FP32 array with the next piece of its branch, so the chunks
 // that load them (at different times) do not fetch a sector twice.  The
 // system is unchanged; only the schedule is.
-void cap_branches(std::vector<Br>& bs, int32_t cap, int64_t base) {
+// With `even`, the pieces are instead ceil(len / cap) of near-equal length
+// (the first len % pieces, from the proximal end, one longer), wherever their
+// boundaries fall.
+void cap_branches(std::vector<Br>& bs, int32_t cap, int64_t base, bool even) {
   bool any = false;
   for (auto& b : bs) any |= b.len > cap;
   if (!any) return;
@@ -141,10 +144,13 @@ void cap_branches(std::vector<Br>& bs, int32_t cap, int64_t base) {
     const Br b = bs[j];
     int32_t parent = b.parent < 0 ? -1 : last_piece[(size_t)b.parent];
     const int64_t end = b.first + b.len;
+    const int32_t pieces = (b.len + cap - 1) / cap, plen = b.len / pieces, rem = b.len % pieces;
     int64_t start = b.first;
-    while (start < end) {
+    for (int32_t k = 0; start < end; ++k) {
       int64_t stop = std::min<int64_t>(end, start + cap);
-      if (stop < end) {
+      if (even) {
+        stop = start + plen + (k < rem ? 1 : 0);
+      } else if (stop < end) {
         const int64_t down = stop - (base + stop) % kCutAlign;  // aligned boundary at or below stop
         if (down > start) stop = down;
       }
@@ -165,7 +171,7 @@ void cap_branches(std::vector<Br>& bs, int32_t cap, int64_t base) {
 }  // namespace
 
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,
-                    int sort_by_length, int pack_compartments, int pieces_per_lane, HostPlan& P) {
+                    int sort_by_length, int pack_compartments, int pieces_per_lane, int even_cuts, HostPlan& P) {
   if (n_cells < 0 || (n_cells > 0 && !ncomp)) return HINES_ERR_INVALID_ARG;
   if (pieces_per_lane != 1 && pieces_per_lane != 2) return HINES_ERR_INVALID_ARG;
   P = HostPlan();
@@ -198,7 +204,8 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
   if (split_branches)
     for (int32_t level = 0; split_level(cells, level, split_branches == 2); ++level) {
     }
-  for (int32_t c = 0; c < n_cells; ++c) cap_branches(cells[(size_t)c], kBranchCap, P.cell_off[(size_t)c]);
+  for (int32_t c = 0; c < n_cells; ++c)
+    cap_branches(cells[(size_t)c], kBranchCap, P.cell_off[(size_t)c], even_cuts != 0);
 
   // flatten to global branch ids (cell by cell, by first compartment)
   P.cell_br_off.assign((size_t)n_cells + 1, 0);

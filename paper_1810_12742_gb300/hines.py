@@ -50,7 +50,7 @@ class HinesError(RuntimeError):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("host_only", ctypes.c_int32), ("split_branches", ctypes.c_int32), ("pieces_per_lane", ctypes.c_int32),
                 ("sort_by_length", ctypes.c_int32), ("pack_compartments", ctypes.c_int32),
-                ("reroot", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("reroot", ctypes.c_int32), ("even_cuts", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -105,6 +105,22 @@ def lib():
     return _lib
 
 
+_deferred = []  # plan handles whose release waits for the end of a CUDA-graph capture
+
+
+def _capturing() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available() and torch.cuda.is_current_stream_capturing()
+    except Exception:
+        return False
+
+
+def _release_deferred():
+    while _deferred and not _capturing():
+        lib().hines_plan_destroy(_deferred.pop())
+
+
 def status_string(code: int) -> str:
     return lib().hines_status_string(int(code)).decode()
 
@@ -128,15 +144,18 @@ class Plan:
     arrays with ``pack``, couplings with ``pack_coupling``).  pieces_per_lane:
     branch pieces each warp lane owns in a chunk (1, the default, or 2).
     split_branches: False/0, True/1 (Section 6's split at the batch's level
-    means) or 2 (the same at each cell's own level means)."""
+    means) or 2 (the same at each cell's own level means).  even_cuts: cut
+    long branches into near-equal pieces instead of at multiples of 8."""
 
     def __init__(self, ncomp, parent, split_branches: bool = False, host_only: bool = False, pieces_per_lane: int = 0,
-                 sort_by_length: bool = False, pack_compartments: int = 0, reroot: bool = False):
+                 sort_by_length: bool = False, pack_compartments: int = 0, reroot: bool = False,
+                 even_cuts: bool = False):
         self._h = ctypes.c_void_p()
+        _release_deferred()
         nc = np.ascontiguousarray(ncomp, np.int32)
         pa = np.ascontiguousarray(parent, np.int32)
         opts = PlanOpts(int(host_only), int(split_branches), int(pieces_per_lane), int(sort_by_length),
-                        int(pack_compartments), int(reroot))
+                        int(pack_compartments), int(reroot), int(even_cuts))
         _check(lib().hines_plan_create(ctypes.byref(self._h), nc.size, _np_ptr(nc), _np_ptr(pa), ctypes.byref(opts)),
                "hines_plan_create")
         info = PlanInfo()
@@ -198,8 +217,14 @@ class Plan:
 
     def close(self):
         if self._h:
-            lib().hines_plan_destroy(self._h)
-            self._h = ctypes.c_void_p()
+            h, self._h = self._h, ctypes.c_void_p()
+            if _capturing():
+                # destroying synchronises the device, which would invalidate a
+                # CUDA-graph capture in progress: release it after the capture
+                _deferred.append(h)
+            else:
+                lib().hines_plan_destroy(h)
+        _release_deferred()
 
     def __del__(self):
         try:

@@ -20,6 +20,8 @@ calls, captures them in a CUDA graph and keeps the checkpoints.
 """
 from __future__ import annotations
 
+import weakref
+
 import torch
 
 from . import hines as H
@@ -127,7 +129,11 @@ class RolloutGraphs:
     bit-identical to them."""
 
     def __init__(self, plan: H.Plan, steps: int, dt: float, E: float, theta: int, checkpoint_every: int):
-        self.plan, self.cfg = plan, (steps, dt, E, theta, checkpoint_every)
+        # the plan owns this object (rollout_graphs keeps it on the plan), so
+        # only a weak reference goes back: no reference cycle keeps a plan
+        # alive until the cycle collector frees it at an arbitrary moment
+        self._plan = weakref.ref(plan)
+        self.cfg = (steps, dt, E, theta, checkpoint_every)
         n, nc = plan.n_unknowns, plan.n_cells
         f = dict(dtype=torch.float64, device="cuda")
         self.g, self.u, self.s, self.V0 = (torch.zeros(n, **f) for _ in range(4))
@@ -148,6 +154,10 @@ class RolloutGraphs:
             self._fwd_body()
         with torch.cuda.graph(self.bwd_graph):
             self._bwd_body()
+
+    @property
+    def plan(self):
+        return self._plan()
 
     def _fwd_body(self):
         plan = self.plan

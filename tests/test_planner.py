@@ -73,17 +73,25 @@ def py_split(cells, local=False):
 CAP, LANES, ALIGN = 16, 32, 8
 
 
-def py_cap(bs, base, cap=CAP):
+def py_cap(bs, base, even=False, cap=CAP):
     """Branches longer than cap become chained pieces: from the proximal end,
     each piece reaches the farthest multiple of ALIGN (global natural index,
-    the cell starting at `base`) within cap compartments, or the branch end."""
+    the cell starting at `base`) within cap compartments, or the branch end.
+    even: ceil(len/cap) near-equal pieces instead, the first len % pieces one
+    longer."""
     out, last = [], {}
     for j, b in enumerate(bs):
         parent = -1 if b[2] < 0 else last[b[2]]
         start, end = b[0], b[0] + b[1]
+        pieces = -(-b[1] // cap)
+        plen, rem = divmod(b[1], pieces)
+        k = 0
         while start < end:
             stop = min(end, start + cap)
-            if stop < end:
+            if even:
+                stop = start + plen + (1 if k < rem else 0)
+                k += 1
+            elif stop < end:
                 down = stop - (base + stop) % ALIGN
                 if down > start:
                     stop = down
@@ -201,12 +209,12 @@ def py_hu(ids, rl, sort_by_length, width):
 G = {}
 
 
-def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0, per_lane=1):
+def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0, per_lane=1, even=False):
     off = np.concatenate(([0], np.cumsum(ncomp))).astype(np.int64)
     cells = [py_branches(parent[off[c]:off[c + 1]]) for c in range(len(ncomp))]
     if split:
         cells = py_split(cells, local=split == 2)
-    cells = [py_cap(bs, int(off[c])) for c, bs in enumerate(cells)]
+    cells = [py_cap(bs, int(off[c]), even) for c, bs in enumerate(cells)]
     first, length, pbr, level, cell, order = [], [], [], [], [], []
     base = 0
     for c, bs in enumerate(cells):
@@ -246,12 +254,12 @@ def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0, per_lane=1
     return out
 
 
-def _compare(ncomp, parent, split, sort_by_length=False, pack=0, per_lane=1):
+def _compare(ncomp, parent, split, sort_by_length=False, pack=0, per_lane=1, even=False):
     plan = H.Plan(ncomp, parent, split_branches=split, host_only=True, sort_by_length=sort_by_length,
-                  pack_compartments=pack, pieces_per_lane=per_lane)
+                  pack_compartments=pack, pieces_per_lane=per_lane, even_cuts=even)
     got = plan.export()
     got.update(plan.export_tasks())
-    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split, sort_by_length, pack, per_lane)
+    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split, sort_by_length, pack, per_lane, even)
     assert plan.n_tasks == ref.pop("n_tasks")
     for k in ref:
         assert np.array_equal(got[k], ref[k]), k
@@ -310,13 +318,14 @@ def test_solver_layout_is_a_permutation():
 @pytest.mark.parametrize("sort_by_length", [False, True])
 @pytest.mark.parametrize("pack", [0, -1, 700])
 @pytest.mark.parametrize("per_lane", [1, 2])
-def test_zoo_matches_restatement(split, sort_by_length, pack, per_lane):
+@pytest.mark.parametrize("even", [False, True])
+def test_zoo_matches_restatement(split, sort_by_length, pack, per_lane, even):
     rng = np.random.default_rng(21)
     trees = []
     for n in (1, 2, 5, 33, 250, 5000):
         trees += list(tree_zoo(rng, n).values())
     ncomp = [t.size for t in trees]
-    _compare(ncomp, np.concatenate(trees), split, sort_by_length, pack, per_lane)
+    _compare(ncomp, np.concatenate(trees), split, sort_by_length, pack, per_lane, even)
 
 
 @pytest.mark.parametrize("name", ["fp64_small", "fp64_uniform", "uneven_steps", "adjoint"])
