@@ -650,12 +650,9 @@ struct FactorMode {
       // rows from the distal end: store the reciprocal pivot (or, reusing the
       // factor, read it) and the eliminated right-hand side, then pass the
       // chain on; at the proximal row leave the contribution to the parent
-      T c0v[P], c1v[P];
 #pragma unroll
-      for (int h = 0; h < P; ++h) c0v[h] = c1v[h] = T(0);
-#pragma unroll
-      for (int r = 0; r < kL; ++r) {
-        if (r < L) {
+      for (int r = 0; r < kL - 1; ++r) {
+        if (r < L - 1) {
           const int i = rows.slot(r, me);
 #pragma unroll
           for (int h = 0; h < P; ++h) {
@@ -663,22 +660,34 @@ struct FactorMode {
             const T uk = su[i + h];
             const T rr = kReuse ? sd[i + h] : rcp_solve(D[h]);
             if (!kReuse) sd[i + h] = rr;
+            sb[i + h] = B[h];
             const T f = uk * rr;
-            if (r < L - 1) {
-              sb[i + h] = B[h];
-              const int i1 = rows.slot(r + 1, me + h);
-              if (!kReuse) {
-                D[h] = sd[i1] - f * uk;
-                if (kCable) D[h] -= uk;  // the edge to the chain child
-              }
-              B[h] = sb[i1] - f * B[h];
-            } else if (m.p[h].pcomp >= 0) {
-              sb[i + h] = B[h];
-              c0v[h] = kReuse ? T(0) : (kCable ? f * uk + uk : f * uk);
-              c1v[h] = f * B[h];
-            } else {
-              sb[i + h] = B[h] * rr;  // solve root
+            const int i1 = rows.slot(r + 1, me + h);
+            if (!kReuse) {
+              D[h] = sd[i1] - f * uk;
+              if (kCable) D[h] -= uk;  // the edge to the chain child
             }
+            B[h] = sb[i1] - f * B[h];
+          }
+        }
+      }
+      T c0v[P], c1v[P];
+      {
+        const int i = rows.slot(L - 1, me);
+#pragma unroll
+        for (int h = 0; h < P; ++h) {
+          c0v[h] = c1v[h] = T(0);
+          if (m.p[h].len == 0) continue;
+          const T uk = su[i + h];
+          const T rr = kReuse ? sd[i + h] : rcp_solve(D[h]);
+          if (!kReuse) sd[i + h] = rr;
+          if (m.p[h].pcomp >= 0) {
+            const T f = uk * rr;
+            sb[i + h] = B[h];
+            c0v[h] = kReuse ? T(0) : (kCable ? f * uk + uk : f * uk);
+            c1v[h] = f * B[h];
+          } else {
+            sb[i + h] = B[h] * rr;  // solve root
           }
         }
       }
@@ -778,7 +787,9 @@ struct RefineMode {
   // x as pairs (two words per slot; FP32 x uses the first)
   static constexpr int kTab = 6 * G::kSlots * 4;
   static constexpr int kStageBytes = kTab + 80;
-  static constexpr int kStages = 1;
+  // the steps stream more arrays than they compute on: two staging buffers
+  // (the next chunk's loads overlap this one's arithmetic) at one piece per lane
+  static constexpr int kStages = P == 1 ? 2 : 1;
   static constexpr int kCslot = 0, kCx = 2 * G::kChunk * 16;
   static constexpr int kCacheBytes = kCx + 2 * G::kChunk * 8;
   static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
