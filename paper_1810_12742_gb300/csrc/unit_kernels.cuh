@@ -787,9 +787,11 @@ struct RefineMode {
   // x as pairs (two words per slot; FP32 x uses the first)
   static constexpr int kTab = 6 * G::kSlots * 4;
   static constexpr int kStageBytes = kTab + 80;
-  // the steps stream more arrays than they compute on: two staging buffers
-  // (the next chunk's loads overlap this one's arithmetic) at one piece per lane
-  static constexpr int kStages = P == 1 ? 2 : 1;
+  // one staging buffer: six staged arrays per chunk, and twice as many warps
+  // per SM hide the loads better than a second buffer at half the warps
+  // (measured on the 228M-compartment batch: 12.6 ms against 13.7 ms per
+  // one-step solve)
+  static constexpr int kStages = 1;
   static constexpr int kCslot = 0, kCx = 2 * G::kChunk * 16;
   static constexpr int kCacheBytes = kCx + 2 * G::kChunk * 8;
   static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
