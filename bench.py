@@ -63,7 +63,9 @@ def parse():
     ap.add_argument("--cable-steps", type=int, default=1000,
                     help="passive-cable steps per captured graph for the time-stepping figure (0: skip)")
     ap.add_argument("--per-lane", type=int, default=0, choices=[0, 1, 2],
-                    help="branch pieces per warp lane of the plan (0: the library's default)")
+                    help="branch pieces per warp lane of every plan (0: the tuned or default options)")
+    ap.add_argument("--untuned", action="store_true",
+                    help="build every plan with the default options instead of the tuned ones")
     ap.add_argument("--only", choices=["headline", "solver_layout"],
                     help="run only this solve, warmup + steps times, and print its time (small profiling runs)")
     return ap.parse_args()
@@ -439,9 +441,30 @@ def main():
     def max_over_ranks(v):
         return reduce_max(v, world, "cuda")
 
+    # Each solve runs on the plan options the autotuner chose for this
+    # morphology on a GB300 (the cache shipped with the package; nothing is
+    # tuned here).  A cache miss, --untuned or --per-lane: default options.
+    from paper_1810_12742_gb300 import autotune as AT
+    plans, plan_options = {}, {}
+
+    def plan_for(solve, layout):
+        opts = None
+        if args.per_lane:
+            opts = {"pieces_per_lane": args.per_lane}
+        elif not args.untuned:
+            opts = AT.cached_options(pop["ncomp"], pop["parent"], solve, layout)
+        plan_options[f"{solve}/{layout}"] = {"options": opts or {}, "tuned": opts is not None and not args.per_lane}
+        key = json.dumps(opts or {}, sort_keys=True)
+        if key not in plans:
+            t0 = time.perf_counter()
+            plans[key] = H.Plan(pop["ncomp"], pop["parent"], **(opts or {}))
+            plan_options[f"{solve}/{layout}"]["plan_create_s"] = time.perf_counter() - t0
+        return plans[key]
+
     t_plan = time.perf_counter()
-    plan = H.Plan(pop["ncomp"], pop["parent"], pieces_per_lane=args.per_lane)
+    plan = plan_for("compensated", "natural")
     config["plan_create_s"] = time.perf_counter() - t_plan  # host planner + upload, once per morphology
+    config["plan_options"] = plan_options
     f32 = {k: torch.as_tensor(pop[k].astype(np.float32)).cuda() for k in ("d", "u", "b")}
     x = torch.empty(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -451,7 +474,8 @@ def main():
 
     if args.only:
         if args.only == "solver_layout":
-            pk = {k: H.pack(plan, f32[k]) for k in ("d", "u", "b")}
+            plan = plan_for("compensated", "solver")
+            pk = {"d": H.pack(plan, f32["d"]), "u": H.pack_coupling(plan, f32["u"]), "b": H.pack(plan, f32["b"])}
             xpk = torch.empty(plan.n_packed, dtype=torch.float64, device="cuda")
 
             def step():  # noqa: F811
@@ -522,6 +546,7 @@ def main():
         return max_over_ranks(float(np.mean(ms)))
 
     # FP64 solve of the same batch (in place; b is restored outside the timed events)
+    plan64 = plan_for("f64", "natural")
     f64 = {k: torch.as_tensor(pop[k]).cuda() for k in ("d", "u", "b")}
     x64 = torch.empty_like(f64["b"])
     ms64 = []
@@ -529,7 +554,7 @@ def main():
         x64.copy_(f64["b"])
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        H.solve(plan, f64["d"], f64["u"], x64)
+        H.solve(plan64, f64["d"], f64["u"], x64)
         a1.record(stream)
         torch.cuda.synchronize()
         if it >= args.warmup:
@@ -543,20 +568,24 @@ def main():
     # with the FP32 factor, and one that substitutes the correction
     xr = torch.empty(n, dtype=torch.float64, device="cuda")
     refine = {}
+    plan_r = plan_for("refine", "natural")
     for st in sorted({1, args.refine_steps}):
-        ms_r = timed(lambda: H.solve_refine(plan, f32["d"], f32["u"], f32["b"], xr, st), args.refine_reps)
+        ms_r = timed(lambda: H.solve_refine(plan_r, f32["d"], f32["u"], f32["b"], xr, st), args.refine_reps)
         refine[st] = (ms_r, max_rel_err(xr, True))
     ms_ref, err_ref = refine[args.refine_steps]
     del xr
 
     # the same solve on arrays kept in the solver layout (Section 5's per-chunk
     # interleaving): what a simulation that stores its state in that layout pays
-    pk = {k: H.pack(plan, f32[k]) for k in ("d", "u", "b")}
-    xpk = torch.empty(plan.n_packed, dtype=torch.float64, device="cuda")
-    ms_pk = timed(lambda: H.solve_compensated_packed(plan, pk["d"], pk["u"], pk["b"], xpk), args.steps)
-    err_pk = max_rel_err(H.unpack(plan, xpk), True)
-    ms_pack = timed(lambda: [H.pack(plan, f32[k], pk[k]) for k in ("d", "u", "b")], 3)
-    ms_unpack = timed(lambda: H.unpack(plan, xpk, x), 3)
+    plan_s = plan_for("compensated", "solver")
+    pk = {"d": H.pack(plan_s, f32["d"]), "u": H.pack_coupling(plan_s, f32["u"]), "b": H.pack(plan_s, f32["b"])}
+    xpk = torch.empty(plan_s.n_packed, dtype=torch.float64, device="cuda")
+    ms_pk = timed(lambda: H.solve_compensated_packed(plan_s, pk["d"], pk["u"], pk["b"], xpk), args.steps)
+    err_pk = max_rel_err(H.unpack(plan_s, xpk), True)
+    ms_pack = timed(lambda: [H.pack(plan_s, f32["d"], pk["d"]), H.pack_coupling(plan_s, f32["u"], pk["u"]),
+                             H.pack(plan_s, f32["b"], pk["b"])], 3)
+    ms_unpack = timed(lambda: H.unpack(plan_s, xpk, x), 3)
+    n_packed_s = plan_s.n_packed
     del pk, xpk
 
     # the same, with every cell re-rooted at its centre (Section 6): couplings
@@ -584,7 +613,8 @@ def main():
                          "full, the others hines_cable_step_reuse (constant matrix, a separate variant)"}
         for layout, reuse in (("natural", False), ("solver", False), ("natural", True), ("solver", True)):
             V = cs["V0"].clone()
-            st = R.CableStepper(plan, cs["s"], cs["g"], cs["u"], V, ws.dt, ws.E, 1, steps=args.cable_steps,
+            st = R.CableStepper(plan_for("cable", layout), cs["s"], cs["g"], cs["u"], V, ws.dt, ws.E, 1,
+                                steps=args.cable_steps,
                                 layout=layout, reuse_factor=reuse)
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(stream)
@@ -611,7 +641,8 @@ def main():
     host = {k: torch.as_tensor(pop[k].astype(np.float32)).pin_memory() for k in ("d", "u", "b")}
     xh = torch.empty(n, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
-    pipe = H.HostPipeline(pop["ncomp"], pop["parent"], pieces=args.e2e_pieces)
+    pipe = H.HostPipeline(pop["ncomp"], pop["parent"], pieces=args.e2e_pieces,
+                          **plan_options["compensated/natural"]["options"])
     e2e_ms = timed(lambda: pipe.solve_compensated(host["d"], host["u"], host["b"], xh), args.e2e_steps)
     e2e_err = max_rel_err(xh.numpy(), True)
     del pipe
@@ -637,7 +668,7 @@ def main():
                  "speedup_of_compensated": ms64 / ms_step},
         "solver_layout": {"value": n / (ms_pk * 1e-3), "unit": "compartments/s", "ms_per_solve": ms_pk,
                           "traffic": None if tr_pk is None else tr_pk * n,
-                          "max_rel_err": err_pk, "n_packed": plan.n_packed,
+                          "max_rel_err": err_pk, "n_packed": n_packed_s,
                           "roofline_frac": BYTES_F32_IN * n / (ms_pk * 1e-3) / 1e9 / peak,
                           "pack_d_u_b_ms": ms_pack, "unpack_x_ms": ms_unpack,
                           "path": "hines_solve_compensated_packed on d, u, b, x kept in the solver layout",

@@ -79,7 +79,9 @@ typedef struct {
   int32_t pack_compartments; /* warp tasks are filled with units up to this many compartments
                                 (0: 24576, or total / 2048 for smaller batches, so that they still
                                 give one task per warp); -1: Section 4's rule instead (a unit joins a task
-                                while every level of the task holds at most 32 branches) */
+                                while every level of the task holds at most a chunk of branches).
+                                Applies to the subtrees of large cells, and to whole cells unless
+                                pack_whole is set */
   int32_t reroot;          /* 1: re-root every cell at its centre (Section 6, balancing the
                               dependency tree; see hines_plan_export_reroot).  Such a plan
                               numbers compartments its own way and takes solver-layout
@@ -91,6 +93,9 @@ typedef struct {
                               farthest multiple of 8 (natural layout) within 16 compartments, so
                               that pieces share no 32-byte sector; 1: into ceil(len / 16) pieces
                               of near-equal length, wherever their boundaries fall */
+  int32_t pack_whole;      /* the same fill for tasks of whole cells (cells of at most 4096
+                              compartments; the other size class is the subtrees of larger cells):
+                              0 as pack_compartments, a count, or -1 for Section 4's rule */
   int32_t reserved[1];     /* must be zero */
 } hines_plan_opts;
 

@@ -183,6 +183,7 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
   if (o.reserved[0] != 0) return HINES_ERR_INVALID_ARG;
+  if (o.pack_whole < -1) return HINES_ERR_INVALID_ARG;
   if (o.even_cuts != 0 && o.even_cuts != 1) return HINES_ERR_INVALID_ARG;
   if (o.pack_compartments < -1) return HINES_ERR_INVALID_ARG;
   if (o.pieces_per_lane == 0) o.pieces_per_lane = 1;
@@ -196,7 +197,7 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
     if (rc == HINES_OK)
       rc = hines::build_host_plan(n_cells, ncomp, p->rerooted ? p->rr.parent.data() : parent, o.split_branches,
                                   o.sort_by_length, o.pack_compartments, o.pieces_per_lane, o.even_cuts,
-                                  p->host);
+                                  o.pack_whole, p->host);
     if (rc == HINES_OK && p->rerooted) {
       // the solver layout maps straight to the caller's numbering: node arrays
       // through the renumbering, couplings through the edge map

@@ -171,7 +171,8 @@ void cap_branches(std::vector<Br>& bs, int32_t cap, int64_t base, bool even) {
 }  // namespace
 
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,
-                    int sort_by_length, int pack_compartments, int pieces_per_lane, int even_cuts, HostPlan& P) {
+                    int sort_by_length, int pack_compartments, int pieces_per_lane, int even_cuts, int pack_whole,
+                    HostPlan& P) {
   if (n_cells < 0 || (n_cells > 0 && !ncomp)) return HINES_ERR_INVALID_ARG;
   if (pieces_per_lane != 1 && pieces_per_lane != 2) return HINES_ERR_INVALID_ARG;
   P = HostPlan();
@@ -344,13 +345,14 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
   // more than 32 branches become several chunks), or, with the lane rule,
   // while every relative level holds at most kLanes branches (Section 4's
   // rule with the 32 lanes of a warp)
-  const bool lane_rule = pack_compartments < 0;
+  // The fill is chosen per size class: whole cells (pack_whole, or as the
+  // subtrees when 0) and the subtrees of large cells (pack_compartments).
   // default fill: kTaskCompartments, but small enough that a small batch
   // still gives kMinTasks tasks (one per warp of a full GPU) where its units allow
-  const int64_t pack_max =
-      pack_compartments > 0
-          ? pack_compartments
-          : std::min<int64_t>(kTaskCompartments, std::max<int64_t>(1, (P.n_unknowns + kMinTasks - 1) / kMinTasks));
+  const int64_t pack_default =
+      std::min<int64_t>(kTaskCompartments, std::max<int64_t>(1, (P.n_unknowns + kMinTasks - 1) / kMinTasks));
+  auto fill_of = [&](int32_t opt) { return opt > 0 ? (int64_t)opt : pack_default; };
+  const int32_t whole_opt = pack_whole != 0 ? pack_whole : pack_compartments;
   P.n_tasks = 0;
   P.task_kind.clear();
   P.task_nlvl.clear();
@@ -361,6 +363,9 @@ int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent
   P.br_task.assign((size_t)nb, -1);
   std::vector<int64_t> task_size;
   for (int32_t kind = 0; kind < 3; ++kind) {
+    const int32_t opt = kind == 0 ? whole_opt : pack_compartments;
+    const bool lane_rule = opt < 0;
+    const int64_t pack_max = fill_of(opt);
     std::vector<int32_t> us;
     for (size_t u = 0; u < units.size(); ++u)
       if (units[u].kind == kind) us.push_back((int32_t)u);

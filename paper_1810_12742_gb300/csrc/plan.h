@@ -90,6 +90,6 @@ constexpr int64_t kMinTasks = 2048;           // smaller tasks for batches below
 // Return codes follow hines_status.
 int build_host_plan(int32_t n_cells, const int32_t* ncomp, const int32_t* parent, int split_branches,
                     int sort_by_length, int pack_compartments, int pieces_per_lane, int even_cuts,
-                    HostPlan& out);
+                    int pack_whole, HostPlan& out);
 
 }  // namespace hines

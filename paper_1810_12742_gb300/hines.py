@@ -50,7 +50,8 @@ class HinesError(RuntimeError):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("host_only", ctypes.c_int32), ("split_branches", ctypes.c_int32), ("pieces_per_lane", ctypes.c_int32),
                 ("sort_by_length", ctypes.c_int32), ("pack_compartments", ctypes.c_int32),
-                ("reroot", ctypes.c_int32), ("even_cuts", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("reroot", ctypes.c_int32), ("even_cuts", ctypes.c_int32), ("pack_whole", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -145,17 +146,19 @@ class Plan:
     branch pieces each warp lane owns in a chunk (1, the default, or 2).
     split_branches: False/0, True/1 (Section 6's split at the batch's level
     means) or 2 (the same at each cell's own level means).  even_cuts: cut
-    long branches into near-equal pieces instead of at multiples of 8."""
+    long branches into near-equal pieces instead of at multiples of 8.
+    pack_compartments / pack_whole: warp-task fill for the subtrees of large
+    cells / for whole cells (0: as pack_compartments)."""
 
     def __init__(self, ncomp, parent, split_branches: bool = False, host_only: bool = False, pieces_per_lane: int = 0,
                  sort_by_length: bool = False, pack_compartments: int = 0, reroot: bool = False,
-                 even_cuts: bool = False):
+                 even_cuts: bool = False, pack_whole: int = 0):
         self._h = ctypes.c_void_p()
         _release_deferred()
         nc = np.ascontiguousarray(ncomp, np.int32)
         pa = np.ascontiguousarray(parent, np.int32)
         opts = PlanOpts(int(host_only), int(split_branches), int(pieces_per_lane), int(sort_by_length),
-                        int(pack_compartments), int(reroot), int(even_cuts))
+                        int(pack_compartments), int(reroot), int(even_cuts), int(pack_whole))
         _check(lib().hines_plan_create(ctypes.byref(self._h), nc.size, _np_ptr(nc), _np_ptr(pa), ctypes.byref(opts)),
                "hines_plan_create")
         info = PlanInfo()
@@ -489,9 +492,10 @@ class HostPipeline:
     streams, so that piece k is solved while piece k+1 arrives and piece k-1
     leaves.  ``solve_compensated`` takes pinned host tensors in the natural
     layout of the whole batch and returns when the work is enqueued on the
-    current stream (which waits for all of it)."""
+    current stream (which waits for all of it).  plan_options go to every
+    piece's plan."""
 
-    def __init__(self, ncomp, parent, pieces: int = 8):
+    def __init__(self, ncomp, parent, pieces: int = 8, **plan_options):
         torch = _torch()
         nc = np.ascontiguousarray(ncomp, np.int64)
         pa = np.ascontiguousarray(parent, np.int32)
@@ -504,7 +508,7 @@ class HostPipeline:
         self.parts = []
         for c0, c1 in zip(bounds[:-1], bounds[1:]):
             lo, hi = int(off[c0]), int(off[c1])
-            plan = Plan(nc[c0:c1], pa[lo:hi])
+            plan = Plan(nc[c0:c1], pa[lo:hi], **plan_options)
             n = hi - lo
             bufs = tuple(torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)) + (
                 torch.empty(n, dtype=torch.float64, device="cuda"),)

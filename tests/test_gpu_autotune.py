@@ -67,3 +67,36 @@ def test_tune_solver_layout_with_rerooted_candidates(tmp_path):
     assert cell_rel_err(H.unpack(plan, xp).cpu().numpy(), ref, pop["offsets"]).max() <= 1e-10
     with pytest.raises(ValueError):
         T.tune_plan(pop["ncomp"], pop["parent"], layout="natural", candidates=cands)
+
+
+@pytest.mark.parametrize("solve,layout", [("compensated", "natural"), ("refine", "natural"), ("cable", "solver"),
+                                          ("f64", "natural")])
+def test_search_tunes_every_option_and_meets_the_gate(tmp_path, solve, layout):
+    """The default search visits every option of the space (per size class
+    fills, lane mapping, cut rule, split, order; re-rooting in the solver
+    layout), keeps the fastest, caches it, and the tuned plan still solves to
+    the mode's tolerance against the oracle."""
+    pop = uneven_subset()
+    cache = str(tmp_path / "tune.json")
+    plan, rep = T.tune_plan(pop["ncomp"], pop["parent"], solve, layout, reps=1, cache_path=cache)
+    space = T.SEARCH_SPACE + (T.SOLVER_LAYOUT_SPACE if layout == "solver" else ())
+    assert len(rep["ms"]) >= sum(len(v) for _, v in space) - len(space)
+    assert set(rep["options"]) <= {k for k, _ in space}
+    assert rep["ms"][__import__("json").dumps(rep["options"], sort_keys=True)] == min(rep["ms"].values())
+    again, rep2 = T.tune_plan(pop["ncomp"], pop["parent"], solve, layout, cache_path=cache)
+    assert rep2["cached"] and rep2["options"] == rep["options"]
+    untuned, rep3 = T.tune_plan(pop["ncomp"], pop["parent"], solve, layout, cache_path=str(tmp_path / "none.json"),
+                                tune_on_miss=False)
+    assert rep3["options"] is None and not rep3["cached"]
+    if solve in ("compensated", "refine") and layout == "natural":
+        f32 = {k: pop[k].astype(np.float32) for k in ("d", "u", "b")}
+        args = [dev(f32[k], torch.float32) for k in ("d", "u", "b")]
+        x = (H.solve_compensated(again, *args) if solve == "compensated"
+             else H.solve_refine(again, *args, steps=1)).cpu().numpy()
+        ref = oracle.solve_batch(pop["ncomp"], pop["parent"], *(f32[k].astype(np.float64) for k in ("d", "u", "b")))
+        assert cell_rel_err(x, ref, pop["offsets"]).max() <= 1e-10
+    if solve == "f64":
+        x = dev(pop["b"])
+        H.solve(again, dev(pop["d"]), dev(pop["u"]), x)
+        ref = oracle.solve_batch(pop["ncomp"], pop["parent"], pop["d"], pop["u"], pop["b"])
+        assert cell_rel_err(x.cpu().numpy(), ref, pop["offsets"]).max() <= 1e-12

@@ -140,13 +140,15 @@ def py_units(ncomp, cells_flat):
     return units
 
 
-def py_tasks(ncomp, units, sort_by_length, pack=24576, width=32):
+def py_tasks(ncomp, units, sort_by_length, pack=24576, width=32, pack_whole=None):
     rl = {}
     for kind, c, root, ids in units:
         for b in ids:
             rl[b] = G["level"][b] - G["level"][root]
     tasks = []
+    pack_subtrees = pack
     for kind in (0, 1, 2):
+        pack = pack_whole if (kind == 0 and pack_whole is not None) else pack_subtrees
         us = [u for u in units if u[0] == kind]
         if kind == 1:  # subtrees packed per cell
             us.sort(key=lambda u: (u[1], -sum(G["len"][b] for b in u[3]), u[2]))
@@ -209,7 +211,7 @@ def py_hu(ids, rl, sort_by_length, width):
 G = {}
 
 
-def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0, per_lane=1, even=False):
+def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0, per_lane=1, even=False, pack_whole=0):
     off = np.concatenate(([0], np.cumsum(ncomp))).astype(np.int64)
     cells = [py_branches(parent[off[c]:off[c + 1]]) for c in range(len(ncomp))]
     if split:
@@ -235,9 +237,11 @@ def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0, per_lane=1
     base_of = np.concatenate(([0], np.cumsum([len(bs) for bs in cells]))).astype(np.int64)
     cells_flat = [list(range(base_of[c], base_of[c + 1])) for c in range(len(cells))]
     units = py_units(list(ncomp), cells_flat)
-    if pack == 0:  # default: 24576, smaller so that a small batch gives 2048 tasks where units allow
-        pack = min(24576, max(1, -(-int(np.sum(ncomp)) // 2048)))
-    tasks = py_tasks(list(ncomp), units, sort_by_length, pack, LANES * per_lane)
+    default = min(24576, max(1, -(-int(np.sum(ncomp)) // 2048)))  # smaller for small batches
+    whole = pack_whole if pack_whole != 0 else pack
+    pack = default if pack == 0 else pack
+    whole = default if whole == 0 else whole
+    tasks = py_tasks(list(ncomp), units, sort_by_length, pack, LANES * per_lane, whole)
     nb = len(first)
     branch_task = np.full(nb, -1, np.int64)
     branch_kind = np.zeros(nb, np.int64)
@@ -254,12 +258,12 @@ def py_plan(ncomp, parent, split=False, sort_by_length=False, pack=0, per_lane=1
     return out
 
 
-def _compare(ncomp, parent, split, sort_by_length=False, pack=0, per_lane=1, even=False):
+def _compare(ncomp, parent, split, sort_by_length=False, pack=0, per_lane=1, even=False, pack_whole=0):
     plan = H.Plan(ncomp, parent, split_branches=split, host_only=True, sort_by_length=sort_by_length,
-                  pack_compartments=pack, pieces_per_lane=per_lane, even_cuts=even)
+                  pack_compartments=pack, pieces_per_lane=per_lane, even_cuts=even, pack_whole=pack_whole)
     got = plan.export()
     got.update(plan.export_tasks())
-    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split, sort_by_length, pack, per_lane, even)
+    ref = py_plan(np.asarray(ncomp), np.asarray(parent), split, sort_by_length, pack, per_lane, even, pack_whole)
     assert plan.n_tasks == ref.pop("n_tasks")
     for k in ref:
         assert np.array_equal(got[k], ref[k]), k
@@ -326,6 +330,15 @@ def test_zoo_matches_restatement(split, sort_by_length, pack, per_lane, even):
         trees += list(tree_zoo(rng, n).values())
     ncomp = [t.size for t in trees]
     _compare(ncomp, np.concatenate(trees), split, sort_by_length, pack, per_lane, even)
+
+
+@pytest.mark.parametrize("pack,pack_whole", [(0, 0), (9000, 3000), (-1, 5000), (12000, -1)])
+def test_size_class_packing_matches_restatement(pack, pack_whole):
+    w = I.WORKLOADS["uneven_steps"]
+    cls = I.cell_classes(w)
+    cells = np.concatenate([np.nonzero(cls == 0)[0][:30], np.nonzero(cls == 1)[0][:3]])
+    ncomp, parent = I.population_trees(w, cells)
+    _compare(ncomp, parent, 0, pack=pack, pack_whole=pack_whole)
 
 
 @pytest.mark.parametrize("name", ["fp64_small", "fp64_uniform", "uneven_steps", "adjoint"])
