@@ -222,20 +222,29 @@ def other_configs(torch, H, oracle, stream, max_over_ranks):
             refs.append(oracle.solve_batch(pop["ncomp"][c:c + 1], pop["parent"][sl], *arrs))
         return refs
 
+    from paper_1810_12742_gb300 import autotune as AT
+
+    def tuned(pop, solve, layout, **extra):
+        """A plan with the cached tuned options of this morphology (defaults on a miss)."""
+        opts = dict(AT.cached_options(pop["ncomp"], pop["parent"], solve, layout) or {}, **extra)
+        return H.Plan(pop["ncomp"], pop["parent"], **opts), opts
+
     # 64 binary cells x 248 compartments, FP64: launch/latency bound
     pop = I.population("fp64_small")
-    plan = H.Plan(pop["ncomp"], pop["parent"])
+    plan, opts_small = tuned(pop, "f64", "natural")
     d, u, b = (torch.as_tensor(pop[k]).cuda() for k in ("d", "u", "b"))
     x = b.clone()
     us = max_over_ranks(_timed_ms(torch, stream, lambda: H.solve(plan, d, u, x), 200) * 1e3)
     x = b.clone()
     H.solve(plan, d, u, x)
     cells = np.arange(pop["ncomp"].size)
-    out["fp64_small"] = {"us_per_solve": us, "compartments": int(pop["offsets"][-1]),
+    out["fp64_small"] = {"us_per_solve": us, "compartments": int(pop["offsets"][-1]), "plan_options": opts_small,
                          "max_rel_err": _cell_err(x.cpu().numpy(), oracle_cells(pop, cells), pop["offsets"], cells)}
-    # solver layout, as built and re-rooted at the centres (Section 6): the
+    # solver layout, tuned, and re-rooted at the centres (Section 6): the
     # critical path of a warp is the depth of its cells
-    for tag, pl in (("solver_layout", plan), ("rerooted", H.Plan(pop["ncomp"], pop["parent"], reroot=True))):
+    plan_sl, opts_sl = tuned(pop, "f64", "solver")
+    out["fp64_small"]["plan_options_solver_layout"] = opts_sl
+    for tag, pl in (("solver_layout", plan_sl), ("rerooted", H.Plan(pop["ncomp"], pop["parent"], reroot=True))):
         dp, up_, xp = H.pack(pl, d), H.pack_coupling(pl, u), H.pack(pl, b)
         xs = xp.clone()
         us_t = max_over_ranks(_timed_ms(torch, stream, lambda: H.solve_packed(pl, dp, up_, xs), 200) * 1e3)
@@ -249,7 +258,7 @@ def other_configs(torch, H, oracle, stream, max_over_ranks):
     # 16384 cells, about 59M compartments, FP64
     pop = I.population("fp64_uniform")
     n1 = int(pop["offsets"][-1])
-    plan = H.Plan(pop["ncomp"], pop["parent"])
+    plan, opts_uni = tuned(pop, "f64", "natural")
     d, u, b = (torch.as_tensor(pop[k]).cuda() for k in ("d", "u", "b"))
     x = b.clone()
     ms = max_over_ranks(_timed_ms(torch, stream, lambda: H.solve(plan, d, u, x), 10))
@@ -257,6 +266,7 @@ def other_configs(torch, H, oracle, stream, max_over_ranks):
     H.solve(plan, d, u, x)
     cells = np.sort(np.random.default_rng(2).choice(pop["ncomp"].size, 32, replace=False))
     out["fp64_uniform"] = {"ms_per_solve": ms, "compartments": n1, "compartments_per_s": n1 / (ms * 1e-3),
+                           "plan_options": opts_uni,
                            "hbm_frac_32B": 32 * n1 / (ms * 1e-3) / 1e9 / peak,
                            "max_rel_err": _cell_err(x.cpu().numpy(), oracle_cells(pop, cells), pop["offsets"], cells)}
     del plan, d, u, b, x, pop
@@ -326,7 +336,7 @@ def other_configs(torch, H, oracle, stream, max_over_ranks):
     # adjoint: 256 cells, 200 implicit-Euler steps, checkpoints every 20
     w = I.WORKLOADS["adjoint"]
     pop = I.population(w, keys=("s", "a", "u", "g", "V0", "target"))
-    plan = H.Plan(pop["ncomp"], pop["parent"])
+    plan, opts_adj = tuned(pop, "cable", "natural")
     tt = {k: torch.as_tensor(pop[k]).cuda() for k in ("s", "a", "g", "V0", "target")}
 
     def rollout_once():
@@ -357,7 +367,7 @@ def other_configs(torch, H, oracle, stream, max_over_ranks):
     roots = pop["offsets"][:-1]
     mask = np.ones(gaa.size, bool)
     mask[roots] = False
-    out["adjoint"] = {"steps": w.steps, "compartments": int(pop["offsets"][-1]),
+    out["adjoint"] = {"steps": w.steps, "compartments": int(pop["offsets"][-1]), "plan_options": opts_adj,
                       "forward_ms": fwd_ms, "backward_ms": bwd_ms, "repeats": len(runs),
                       "timing": "median of 5 after 2 warm-up rollouts (CUDA events); the first rollout builds "
                                 "and captures the forward and reverse graphs",

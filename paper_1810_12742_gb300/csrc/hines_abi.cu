@@ -115,8 +115,9 @@ hines_status upload(hines_plan_t p) {
   const size_t fac_b = align256(std::max(n, (size_t)H.n_packed) * 8 + 8), cd_b = align256(nb * 16 + 16),
                cb_b = align256(nb * 32 + 32),
                ds_b = align256(nb * 16 + 16), xl_b = align256(nb * 8 + 8), red_b = align256(nc * 8 + 8),
-               cnt_b = align256((nc + 4) * 4), rw_b = align256(std::max(n, (size_t)H.n_packed) * 4 + 4);
-  const size_t wtotal = fac_b + cd_b + cb_b + ds_b + xl_b + red_b + cnt_b + rw_b;
+               cnt_b = align256((nc + 4) * 4), rw_b = align256(std::max(n, (size_t)H.n_packed) * 4 + 4),
+               ff4_b = align256((size_t)H.n_packed * 16 + 16);
+  const size_t wtotal = fac_b + cd_b + cb_b + ds_b + xl_b + red_b + cnt_b + rw_b + ff4_b;
   if (cudaMalloc(&p->work, wtotal) != cudaSuccess) {
     cudaGetLastError();
     p->work = nullptr;
@@ -140,6 +141,8 @@ hines_status upload(hines_plan_t p) {
   D.cell_pending = D.counter + 4;
   w += cnt_b;
   D.rw = w;
+  w += rw_b;
+  D.ff4 = w;
   D.n_wtasks = H.n_tasks;
   D.per_lane = H.per_lane;
   D.n_packed = H.n_packed;

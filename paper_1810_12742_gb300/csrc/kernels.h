@@ -65,6 +65,7 @@ struct DevPlan {
   void* xlast = nullptr;  // n_branches * 8 bytes: solution at the distal compartment per position
   void* red = nullptr;    // n_cells * 8 bytes: per-cell reductions
   void* rw = nullptr;     // 4 bytes per natural or solver-layout slot: the refinement's eliminated residual
+  void* ff4 = nullptr;    // 16 bytes per solver-layout slot: the compensated solve's factor (y, g as pairs)
   int32_t* status = nullptr;  // device status word
 };
 

@@ -81,14 +81,18 @@ struct Piece {
 };
 template <int P>
 struct Meta {
+  long long blk;  // the chunk's block offset in the solver layout
   Piece p[P];
   float4 ds[P];  // compensated substitution: folded distal state left by the elimination
   int L;         // rows of the lane: length of its first (longer) piece, 0 for a lane without pieces
 };
 
 template <bool kPk, int P>
-__device__ __forceinline__ Meta<P> load_meta(const DevPlan& Pl, int c0, int n, int lane, bool active, bool want_ds) {
+__device__ __forceinline__ Meta<P> load_meta(const DevPlan& Pl, int c0, int n, int lane, bool active, bool want_ds,
+                                             bool want_blk = false) {
   Meta<P> m;
+  m.blk = 0;
+  if (want_blk && active && n > 0) m.blk = Pl.pk_meta[c0].x;  // every piece of a chunk shares it
 #pragma unroll
   for (int h = 0; h < P; ++h) {
     const int i = P * lane + h;
@@ -221,16 +225,21 @@ __device__ __forceinline__ F2 vset_hi(F2 v, float w) { return f2_make(f2_lo(v), 
 
 // ============================================================================
 // Compensated mode: FP32 inputs, double-float arithmetic from FP32 error-free
-// transformations, FP64 solution.  The elimination keeps nothing per
-// compartment: it leaves, per piece, its contribution to the parent (or the
-// root's solution) and its folded distal state; the substitution re-stages the
-// chunk and re-eliminates it from that state before substituting.
+// transformations, FP64 solution.  The elimination leaves, per compartment k,
+// the two double-float numbers the substitution needs, y_k = B_k / D_k and
+// g_k = u_k / D_k (D, B: the eliminated pivot and right-hand side), written
+// in the chunk's block order of the solver layout (16 bytes a slot, each row
+// a contiguous run); per piece its contribution to the parent.  The
+// substitution stages the block with 16-byte copies and runs
+// x_k = y_k - g_k x_{k+1} from the proximal row (x of the parent's distal
+// compartment) to the distal one: no inputs are read again.
 // ============================================================================
 template <bool kPk, int P>
 struct CompMode {
   using V = typename VOf<P>::type;
   using G = Geo<P>;
   static constexpr bool kPacked = kPk;
+  static constexpr bool kNeedsBlk = true;
   static constexpr int kPer = P;
   struct Args {
     const float* d;
@@ -238,30 +247,34 @@ struct CompMode {
     const float* b;
     double* x;
   };
-  // a staging buffer: d, u, b, then the chunk's row table (solver layout)
-  static constexpr int kTab = 3 * G::kSlots * 4;
+  // a staging buffer: elimination, d, u, b (3 words a slot); substitution,
+  // the factor block (4 words a slot, the FP64 solution written over its
+  // first two); then the block's row table
+  static constexpr int kArr = 3 * G::kSlots * 4, kFac = G::kSlots * 16;
+  static constexpr int kTab = kArr > kFac ? kArr : kFac;
   static constexpr int kStageBytes = kTab + 80;
-  // two buffers with one piece per lane (the next chunk is staged while this
-  // one is computed); one with two, whose chunks are twice as large
-  static constexpr int kStages = P == 1 ? 2 : 1;
+  static constexpr int kStages = 1;
   static constexpr int kCslot = 0, kCx = 2 * G::kChunk * 16;
   static constexpr int kCacheBytes = kCx + 2 * G::kChunk * 8;
   static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
-  // CTAs per SM that shared memory allows; two pieces per lane need more
-  // registers than eight CTAs leave, so they are held to six
-  static constexpr int kMinBlocks = P == 2 ? 6 : kSmemPerSm / (kWarps * kWarpBytes);
-  static constexpr bool kWantDs = true;
+  static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes) < 12 ? kSmemPerSm / (kWarps * kWarpBytes) : 12;
+  static constexpr bool kWantDs = false;
 
-  __device__ static void stage(const DevPlan&, const Args& A, int, const Meta<P>& m, int n, int lane,
+  __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, const Meta<P>& m, int n, int lane,
                                unsigned char* buf) {
+    int* tab = reinterpret_cast<int*>(buf + kTab);
+    build_row_table<P>(m.L, lane, tab);
+    const int e = tab[kL];
+    if (visit == 1) {
+      stage_block(reinterpret_cast<float4*>(buf), static_cast<const float4*>(Pl.ff4), m.blk, e, lane);
+      cp_commit();
+      return;
+    }
     float* sd = reinterpret_cast<float*>(buf);
     float* su = sd + G::kSlots;
     float* sb = su + G::kSlots;
     if (kPk) {
-      int* tab = reinterpret_cast<int*>(buf + kTab);
-      build_row_table<P>(m.L, lane, tab);
       const long long blk = __shfl_sync(kFull, m.p[0].first, 0);
-      const int e = tab[kL];
       stage_block(sd, A.d, blk, e, lane);
       stage_block(su, A.u, blk, e, lane);
       stage_block(sb, A.b, blk, e, lane);
@@ -278,22 +291,23 @@ struct CompMode {
 
   __device__ static void compute(const DevPlan& Pl, const Args&, int visit, int c0, int n, int lane,
                                  const Meta<P>& m, unsigned char* buf, const Prev& pv, unsigned char* cache, int cur) {
-    float* sd = reinterpret_cast<float*>(buf);
-    float* su = sd + G::kSlots;
-    float* sb = su + G::kSlots;
     float4* cslot = reinterpret_cast<float4*>(cache + kCslot);  // [2][kChunk] contributions
     float2* cx = reinterpret_cast<float2*>(cache + kCx);        // [2][kChunk] distal solutions
-    const Rows<kPk, P> rows{reinterpret_cast<const int*>(buf + kTab)};
+    const int* tab = reinterpret_cast<const int*>(buf + kTab);
     float4* slot = static_cast<float4*>(Pl.cd);
-    float4* dst = static_cast<float4*>(Pl.dstate);
     float2* xlast = static_cast<float2*>(Pl.xlast);
     const int L = m.L;
     if (L == 0) return;
     const int me = P * lane;
     // the second piece's distal row (it joins the chain there); L: none
     const int delta = P == 2 ? L - m.p[P - 1].len : 0;
-    float d0h[P], d0l[P], b0h[P], b0l[P];
     if (visit == 0) {
+      const float* sd = reinterpret_cast<const float*>(buf);
+      const float* su = sd + G::kSlots;
+      const float* sb = su + G::kSlots;
+      float4* fac = static_cast<float4*>(Pl.ff4) + m.blk;
+      const Rows<kPk, P> rows{tab};
+      float d0h[P], d0l[P], b0h[P], b0l[P];
 #pragma unroll
       for (int h = 0; h < P; ++h) {
         const Piece& q = m.p[h];
@@ -309,91 +323,58 @@ struct CompMode {
           Dv = ff_sub(Dv, v.x, v.y);
           Bv = ff_sub(Bv, v.z, v.w);
         }
-        dst[c0 + me + h] = make_float4(Dv.h, Dv.l, Bv.h, Bv.l);
         d0h[h] = Dv.h;
         d0l[h] = Dv.l;
         b0h[h] = Bv.h;
         b0l[h] = Bv.l;
       }
       FFV<V> D{vpack<P>(d0h), vpack<P>(d0l)}, B{vpack<P>(b0h), vpack<P>(b0l)};
+      // row r: g = u / D, y = B / D into the factor block; then the chain to row r + 1
 #pragma unroll
-      for (int r = 1; r < kL; ++r) {
-        if (r < L) {
-          const int i0 = rows.slot(r - 1, me), i1 = rows.slot(r, me);
-          const V uk = ldv(su, i0, V{});
-          const FFV<V> f = vdiv_f(uk, D);
-          const FFV<V> fu = vmul_f(f, uk);
-          const FFV<V> fb = vmul_ff(f, B);
+      for (int r = 0; r < kL - 1; ++r) {
+        if (r < L - 1) {
+          const V uk = ldv(su, rows.slot(r, me), V{});
+          const FFV<V> g = vdiv_f(uk, D);
+          const FFV<V> y = vdiv(B, D);
+          const int f0 = tab[r] + me;
+#pragma unroll
+          for (int h = 0; h < P; ++h)
+            fac[f0 + h] = make_float4(vget(y.h, h), vget(y.l, h), vget(g.h, h), vget(g.l, h));
+          const FFV<V> fu = vmul_f(g, uk);
+          const FFV<V> fb = vmul_ff(g, B);
+          const int i1 = rows.slot(r + 1, me);
           D = vsub_dom(ldv(sd, i1, V{}), fu.h, fu.l);
           B = vsub_ff(ldv(sb, i1, V{}), fb.h, fb.l);
           if constexpr (P == 2) {
-            if (r == delta) {
+            if (r + 1 == delta) {
               D = {vset_hi(D.h, d0h[1]), vset_hi(D.l, d0l[1])};
               B = {vset_hi(B.h, b0h[1]), vset_hi(B.l, b0l[1])};
             }
           }
         }
       }
-      // the proximal row: contribution to the parent, or the root's solution
+      // the proximal row: its factor, and the contribution to the parent (a
+      // root's solution is its y, the factor's first number)
       const V uk = ldv(su, rows.slot(L - 1, me), V{});
-      const FFV<V> f = vdiv_f(uk, D);
-      const FFV<V> fu = vmul_f(f, uk);
-      const FFV<V> fb = vmul_ff(f, B);
-      const FFV<V> x0 = vdiv(B, D);
+      const FFV<V> g = vdiv_f(uk, D);
+      const FFV<V> y = vdiv(B, D);
+      const FFV<V> fu = vmul_f(g, uk);
+      const FFV<V> fb = vmul_ff(g, B);
+      const int f0 = tab[L - 1] + me;
 #pragma unroll
       for (int h = 0; h < P; ++h) {
-        if (m.p[h].len == 0) continue;
-        const float4 out = m.p[h].pcomp >= 0
-                               ? make_float4(vget(fu.h, h), vget(fu.l, h), vget(fb.h, h), vget(fb.l, h))
-                               : make_float4(vget(x0.h, h), vget(x0.l, h), 0.f, 0.f);
+        const bool root = m.p[h].pcomp < 0;  // a cell's root: no coupling to a parent
+        fac[f0 + h] = make_float4(vget(y.h, h), vget(y.l, h), root ? 0.f : vget(g.h, h), root ? 0.f : vget(g.l, h));
+        if (m.p[h].len == 0 || root) continue;
+        const float4 out = make_float4(vget(fu.h, h), vget(fu.l, h), vget(fb.h, h), vget(fb.l, h));
         slot[c0 + me + h] = out;
         cslot[cur * G::kChunk + me + h] = out;
       }
       return;
     }
-    // substitution: re-eliminate from the folded distal state, keeping the
-    // pivots' and right-hand sides' high parts in the staged rows and their
-    // low parts in registers, then substitute from the proximal row
-#pragma unroll
-    for (int h = 0; h < P; ++h) {
-      d0h[h] = m.ds[h].x;
-      d0l[h] = m.ds[h].y;
-      b0h[h] = m.ds[h].z;
-      b0l[h] = m.ds[h].w;
-    }
-    FFV<V> D{vpack<P>(d0h), vpack<P>(d0l)}, B{vpack<P>(b0h), vpack<P>(b0l)};
-    V Dl[kL], Bl[kL];
-    {
-      const int i0 = rows.slot(0, me);
-      stv(sd, i0, D.h);
-      stv(sb, i0, B.h);
-      Dl[0] = D.l;
-      Bl[0] = B.l;
-    }
-#pragma unroll
-    for (int r = 1; r < kL; ++r) {
-      if (r < L) {
-        const int i0 = rows.slot(r - 1, me), i1 = rows.slot(r, me);
-        const V uk = ldv(su, i0, V{});
-        const FFV<V> f = vdiv_f(uk, D);
-        const FFV<V> fu = vmul_f(f, uk);
-        const FFV<V> fb = vmul_ff(f, B);
-        D = vsub_dom(ldv(sd, i1, V{}), fu.h, fu.l);
-        B = vsub_ff(ldv(sb, i1, V{}), fb.h, fb.l);
-        if constexpr (P == 2) {
-          if (r == delta) {
-            D = {vset_hi(D.h, d0h[1]), vset_hi(D.l, d0l[1])};
-            B = {vset_hi(B.h, b0h[1]), vset_hi(B.l, b0l[1])};
-          }
-        }
-        stv(sd, i1, D.h);
-        stv(sb, i1, B.h);
-        Dl[r] = D.l;
-        Bl[r] = B.l;
-      }
-    }
-    // the parents' distal solutions (a cell's root: none; its coupling is not
-    // part of the system, so it is taken as zero)
+    // substitution: x = y - g x_parent from the proximal row down; the FP64
+    // solution goes over the slot's first two words
+    float4* sf = reinterpret_cast<float4*>(buf);
     float xph[P], xpl[P];
 #pragma unroll
     for (int h = 0; h < P; ++h) {
@@ -404,8 +385,6 @@ struct CompMode {
         const float2 t = (loc >= 0 && loc < pv.n) ? cx[pv.which * G::kChunk + loc] : xlast[q.ppos];
         xph[h] = t.x;
         xpl[h] = t.y;
-      } else if (q.len > 0) {
-        su[rows.slot(L - 1, me + h)] = 0.f;
       }
     }
     FFV<V> X{vpack<P>(xph), vpack<P>(xpl)};
@@ -413,22 +392,26 @@ struct CompMode {
 #pragma unroll
     for (int r = kL - 1; r >= 0; --r) {
       if (r < L) {
-        const int i = rows.slot(r, me);
-        const V uk = ldv(su, i, V{});
-        const FFV<V> M = vmul_f(X, uk);
-        const FFV<V> num = vsub_ffff(FFV<V>{ldv(sb, i, V{}), Bl[r]}, M.h, M.l);
-        X = vdiv(num, FFV<V>{ldv(sd, i, V{}), Dl[r]});
+        const int q = tab[r] + me;
+        float yh[P], yl[P], gh[P], gl[P];
+#pragma unroll
+        for (int h = 0; h < P; ++h) {
+          const float4 f = sf[q + h];
+          yh[h] = f.x;
+          yl[h] = f.y;
+          gh[h] = f.z;
+          gl[h] = f.w;
+        }
+        const FFV<V> gx = vmul_ff(FFV<V>{vpack<P>(gh), vpack<P>(gl)}, X);
+        X = vsub_ffff(FFV<V>{vpack<P>(yh), vpack<P>(yl)}, gx.h, gx.l);
+#pragma unroll
+        for (int h = 0; h < P; ++h)
+          reinterpret_cast<double*>(sf + q + h)[0] = ff_to_double(vget(X.h, h), vget(X.l, h));
         if constexpr (P == 2) {
-          reinterpret_cast<double*>(sd + i)[0] = ff_to_double(f2_lo(X.h), f2_lo(X.l));
-          reinterpret_cast<double*>(sb + i)[0] = ff_to_double(f2_hi(X.h), f2_hi(X.l));
           if (r == delta) {
             xbh = f2_hi(X.h);
             xbl = f2_hi(X.l);
           }
-        } else {
-          const double xd = ff_to_double(X.h, X.l);
-          sd[i] = __int_as_float(__double2loint(xd));
-          sb[i] = __int_as_float(__double2hiint(xd));
         }
       }
     }
@@ -441,29 +424,18 @@ struct CompMode {
     }
   }
 
-  // the FP64 solution of a staged slot (natural layout: piece i at row r)
-  __device__ static double x_at(const float* sd, const float* sb, int q) {
-    if constexpr (P == 2) {
-      return (q & 1) ? reinterpret_cast<const double*>(sb + q - 1)[0] : reinterpret_cast<const double*>(sd + q)[0];
-    } else {
-      return __hiloint2double(__float_as_int(sb[q]), __float_as_int(sd[q]));
-    }
-  }
-
   __device__ static void copy_out(const DevPlan&, const Args& A, int visit, const Meta<P>& m, int n, int lane,
                                   unsigned char* buf) {
     if (visit == 0) return;
-    const float* sd = reinterpret_cast<const float*>(buf);
-    const float* sb = sd + 2 * G::kSlots;
+    const double* sx = reinterpret_cast<const double*>(buf);  // two per slot: the solution, then g
+    const int* tab = reinterpret_cast<const int*>(buf + kTab);
     if (kPk) {
-      const int* tab = reinterpret_cast<const int*>(buf + kTab);
       const long long blk = __shfl_sync(kFull, m.p[0].first, 0);
       const int e = tab[kL];
-      for (int s = lane; s < e; s += 32) A.x[blk + s] = x_at(sd, sb, s);
+      for (int s = lane; s < e; s += 32) A.x[blk + s] = sx[2 * s];
       return;
     }
-    for_chunk_elements(m, n, lane,
-                       [&](int i, int, int row, long long g, bool) { A.x[g] = x_at(sd, sb, nidx<P>(row, i)); });
+    for_chunk_elements(m, n, lane, [&](int i, int, int row, long long g, bool) { A.x[g] = sx[2 * (tab[row] + i)]; });
   }
 };
 
@@ -495,6 +467,7 @@ struct FactorMode {
     return r;
   }
   static constexpr bool kPacked = kPk;
+  static constexpr bool kNeedsBlk = false;
   static constexpr int kPer = P;
   struct Args {
     const T* d;
@@ -773,6 +746,7 @@ struct RefineMode {
   using V = typename VOf<P>::type;
   using G = Geo<P>;
   static constexpr bool kPacked = false;
+  static constexpr bool kNeedsBlk = false;
   static constexpr int kPer = P;
   struct Args {
     const float* d;
@@ -1047,7 +1021,7 @@ __device__ void run_task(const DevPlan& Pl, const typename M::Args& A, int t, in
   unsigned char* cache = wbase + M::kStages * M::kStageBytes;
   auto buf = [wbase](int which) { return wbase + (M::kStages == 2 ? which : 0) * M::kStageBytes; };
   auto meta = [&](const Pos& p) {
-    return load_meta<M::kPacked, P>(Pl, p.c0, p.n, lane, p.visit < ve, M::kWantDs && p.visit == 1);
+    return load_meta<M::kPacked, P>(Pl, p.c0, p.n, lane, p.visit < ve, M::kWantDs && p.visit == 1, M::kNeedsBlk);
   };
   // metadata runs two chunks ahead; with two staging buffers the next chunk
   // is staged while this one is computed, with one right after this one's
@@ -1075,6 +1049,9 @@ __device__ void run_task(const DevPlan& Pl, const typename M::Args& A, int t, in
     M::copy_out(Pl, A, cur.visit, m_cur, cur.n, lane, buf(which));
     __syncwarp();
     if (crossing && nxt.visit < ve) {
+      // the substitution reads what the elimination wrote (through L2)
+      __threadfence();
+      __syncwarp();
       m_nxt = meta(nxt);
       m_nn = meta(nn);
     }
