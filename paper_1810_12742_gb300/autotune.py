@@ -40,7 +40,7 @@ TUNED_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_pl
 # option -> values tried, in the order the search visits them
 SEARCH_SPACE = (
     ("even_cuts", (False, True)),
-    ("pack_compartments", (12288, 24576, 49152)),
+    ("pack_compartments", (6144, 12288, 24576, 49152)),
     ("pack_whole", (0, 6144, 49152)),
     ("pieces_per_lane", (1, 2)),
     ("split_branches", (0, 1, 2)),

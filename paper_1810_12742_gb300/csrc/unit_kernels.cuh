@@ -79,11 +79,27 @@ struct Piece {
                            // block offset, the parent's solver-layout index (-1 at a cell's root)
   int ppos, cpos, len, nchild, ccontig, xtask;
 };
+// A parent's solution fetched ahead: a double-float pair (compensated and
+// refinement modes) or one value of the solve's type (factor modes).
+union PreX {
+  float2 ff;
+  float f;
+  double d;
+};
+__device__ __forceinline__ float pre_get(const PreX& v, float) { return v.f; }
+__device__ __forceinline__ double pre_get(const PreX& v, double) { return v.d; }
+__device__ __forceinline__ void pre_set(PreX& v, float x) { v.f = x; }
+__device__ __forceinline__ void pre_set(PreX& v, double x) { v.d = x; }
+
 template <int P>
 struct Meta {
   long long blk;  // the chunk's block offset in the solver layout
   Piece p[P];
   float4 ds[P];  // compensated substitution: folded distal state left by the elimination
+  // substitution: the parent's solution when another chunk than the cached
+  // predecessor left it, fetched while the chunk is staged so that its
+  // latency overlaps the staging copies
+  PreX xpre[P];
   int L;         // rows of the lane: length of its first (longer) piece, 0 for a lane without pieces
 };
 
@@ -98,6 +114,7 @@ __device__ __forceinline__ Meta<P> load_meta(const DevPlan& Pl, int c0, int n, i
     const int i = P * lane + h;
     Piece q{0, -1, -1, 0, 0, 0, 0, 0};
     m.ds[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+    m.xpre[h].d = 0.0;
     if (active && i < n) {
       const int pos = c0 + i;
       if (want_ds) m.ds[h] = static_cast<const float4*>(Pl.dstate)[pos];
@@ -260,14 +277,22 @@ struct CompMode {
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes) < 12 ? kSmemPerSm / (kWarps * kWarpBytes) : 12;
   static constexpr bool kWantDs = false;
 
-  __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, const Meta<P>& m, int n, int lane,
-                               unsigned char* buf) {
+  __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, Meta<P>& m, int n, int lane,
+                               unsigned char* buf, const Prev& pv) {
     int* tab = reinterpret_cast<int*>(buf + kTab);
     build_row_table<P>(m.L, lane, tab);
     const int e = tab[kL];
     if (visit == 1) {
       stage_block(reinterpret_cast<float4*>(buf), static_cast<const float4*>(Pl.ff4), m.blk, e, lane);
       cp_commit();
+      // the parent's solution, unless the predecessor chunk's cache holds it
+#pragma unroll
+      for (int h = 0; h < P; ++h) {
+        const Piece& q = m.p[h];
+        const int loc = q.ppos - pv.c0;
+        if (q.len > 0 && q.pcomp >= 0 && !(loc >= 0 && loc < pv.n))
+          m.xpre[h].ff = static_cast<const float2*>(Pl.xlast)[q.ppos];
+      }
       return;
     }
     float* sd = reinterpret_cast<float*>(buf);
@@ -382,7 +407,7 @@ struct CompMode {
       xph[h] = xpl[h] = 0.f;
       if (q.len > 0 && q.pcomp >= 0) {
         const int loc = q.ppos - pv.c0;
-        const float2 t = (loc >= 0 && loc < pv.n) ? cx[pv.which * G::kChunk + loc] : xlast[q.ppos];
+        const float2 t = (loc >= 0 && loc < pv.n) ? cx[pv.which * G::kChunk + loc] : m.xpre[h].ff;
         xph[h] = t.x;
         xpl[h] = t.y;
       }
@@ -500,12 +525,23 @@ struct FactorMode {
     return si * fma(A.dt * gi, fma(A.theta - T(1), vi, A.E), vi);
   }
 
-  __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, const Meta<P>& m, int n, int lane,
-                               unsigned char* buf) {
+  __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, Meta<P>& m, int n, int lane,
+                               unsigned char* buf, const Prev& pv) {
     T* sd = reinterpret_cast<T*>(buf);
     T* su = sd + G::kSlots;
     T* sb = su + G::kSlots;
     const T* fac = static_cast<const T*>(Pl.fac);
+    if (visit == 1) {
+      // the parent's solution, unless the predecessor chunk's cache holds it
+      // (a chunk staged before its predecessor is computed finds that
+      // predecessor's solutions in the cache, so it never reads them here)
+#pragma unroll
+      for (int h = 0; h < P; ++h) {
+        const Piece& q = m.p[h];
+        const int loc = q.ppos - pv.c0;
+        if (q.len > 0 && q.pcomp >= 0 && !(loc >= 0 && loc < pv.n)) pre_set(m.xpre[h], A.x[q.pcomp]);
+      }
+    }
     if (kPk) {
       int* tab = reinterpret_cast<int*>(buf + kTab);
       build_row_table<P>(m.L, lane, tab);
@@ -682,7 +718,7 @@ struct FactorMode {
       xp[h] = T(0);
       if (q.len > 0 && q.pcomp >= 0) {
         const int loc = q.ppos - pv.c0;
-        xp[h] = (loc >= 0 && loc < pv.n) ? cx[pv.which * G::kChunk + loc] : A.x[q.pcomp];
+        xp[h] = (loc >= 0 && loc < pv.n) ? cx[pv.which * G::kChunk + loc] : pre_get(m.xpre[h], T{});
       }
     }
 #pragma unroll
@@ -772,14 +808,24 @@ struct RefineMode {
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);
   static constexpr bool kWantDs = false;
 
-  __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, const Meta<P>& m, int n, int lane,
-                               unsigned char* buf) {
+  __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, Meta<P>& m, int n, int lane,
+                               unsigned char* buf, const Prev& pv) {
     float* sd = reinterpret_cast<float*>(buf);
     float* su = sd + G::kSlots;
     float* sb = su + G::kSlots;
     float* sf = sb + G::kSlots;
     float* sx = sf + G::kSlots;  // [2 * kSlots]
     const float* fac = static_cast<const float*>(Pl.fac);
+    if (visit == 1) {
+      // the parent's correction, unless the predecessor chunk's cache holds it
+#pragma unroll
+      for (int h = 0; h < P; ++h) {
+        const Piece& q = m.p[h];
+        const int loc = q.ppos - pv.c0;
+        if (q.len > 0 && q.pcomp >= 0 && !(loc >= 0 && loc < pv.n))
+          m.xpre[h].f = static_cast<const float2*>(Pl.xlast)[q.ppos].x;
+      }
+    }
     for_chunk_elements(m, n, lane, [&](int i, int, int row, long long g, bool) {
       const int q = nidx<P>(row, i);
       if (visit == 0) {
@@ -916,7 +962,7 @@ struct RefineMode {
       cph[h] = 0.f;
       if (q.len > 0 && q.pcomp >= 0) {
         const int loc = q.ppos - pv.c0;
-        cph[h] = (loc >= 0 && loc < pv.n) ? cx[pv.which * G::kChunk + loc] : xlast[q.ppos].x;
+        cph[h] = (loc >= 0 && loc < pv.n) ? cx[pv.which * G::kChunk + loc] : m.xpre[h].f;
       }
     }
     V cp = vpack<P>(cph);
@@ -1028,10 +1074,10 @@ __device__ void run_task(const DevPlan& Pl, const typename M::Args& A, int t, in
   // results are out
   Pos cur = pos_level<W>(vb, vb == 0 ? nl - 1 : 0, lp);
   Meta<P> m_cur = meta(cur);
-  M::stage(Pl, A, cur.visit, m_cur, cur.n, lane, buf(0));
+  Prev pv{0, 0, 0};  // last chunk of the previous level in this sweep
+  M::stage(Pl, A, cur.visit, m_cur, cur.n, lane, buf(0), pv);
   Pos nxt = pos_next<W>(cur, lp, nl, ve);
   Meta<P> m_nxt = meta(nxt);
-  Prev pv{0, 0, 0};  // last chunk of the previous level in this sweep
   int which = 0;
   while (cur.visit < ve) {
     cp_wait_all();
@@ -1040,8 +1086,12 @@ __device__ void run_task(const DevPlan& Pl, const typename M::Args& A, int t, in
     // finished: its first chunks reuse positions the elimination is still
     // writing (and read the folded states it leaves)
     const bool crossing = nxt.visit != cur.visit;
+    // predecessor of the next chunk: the last chunk of the level before its level, same sweep
+    const Prev pn = crossing ? Prev{0, 0, 0} : nxt.l != cur.l ? Prev{cur.c0, cur.n, cur.l & 1} : pv;
+    // (staged before this chunk is computed: a mode with two buffers reads
+    // nothing in stage that this chunk writes)
     if (M::kStages == 2 && nxt.visit < ve && !crossing)
-      M::stage(Pl, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1));
+      M::stage(Pl, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1), pn);
     const Pos nn = nxt.visit < ve ? pos_next<W>(nxt, lp, nl, ve) : nxt;
     Meta<P> m_nn = meta(nn);
     M::compute(Pl, A, cur.visit, cur.c0, cur.n, lane, m_cur, buf(which), pv, cache, cur.l & 1);
@@ -1056,13 +1106,8 @@ __device__ void run_task(const DevPlan& Pl, const typename M::Args& A, int t, in
       m_nn = meta(nn);
     }
     if (nxt.visit < ve && (crossing || M::kStages == 1))
-      M::stage(Pl, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1));
-    // predecessor of the next chunk: the last chunk of the level before its level, same sweep
-    if (crossing) {
-      pv = Prev{0, 0, 0};
-    } else if (nxt.l != cur.l) {
-      pv = Prev{cur.c0, cur.n, cur.l & 1};
-    }
+      M::stage(Pl, A, nxt.visit, m_nxt, nxt.n, lane, buf(which ^ 1), pn);
+    pv = pn;
     cur = nxt;
     m_cur = m_nxt;
     nxt = nn;
