@@ -66,7 +66,7 @@ def parse():
                     help="branch pieces per warp lane of every plan (0: the tuned or default options)")
     ap.add_argument("--untuned", action="store_true",
                     help="build every plan with the default options instead of the tuned ones")
-    ap.add_argument("--only", choices=["headline", "solver_layout"],
+    ap.add_argument("--only", choices=["headline", "solver_layout", "fp64", "cable"],
                     help="run only this solve, warmup + steps times, and print its time (small profiling runs)")
     return ap.parse_args()
 
@@ -490,6 +490,22 @@ def main():
 
             def step():  # noqa: F811
                 H.solve_compensated_packed(plan, pk["d"], pk["u"], pk["b"], xpk)
+        elif args.only == "fp64":
+            plan = plan_for("f64", "natural")
+            f64 = {k: torch.as_tensor(pop[k]).cuda() for k in ("d", "u", "b")}
+            x64 = torch.empty_like(f64["b"])
+
+            def step():  # noqa: F811
+                x64.copy_(f64["b"])
+                H.solve(plan, f64["d"], f64["u"], x64)
+        elif args.only == "cable":  # one passive-cable step (rebuild fused with the FP64 solve), natural layout
+            plan = plan_for("cable", "natural")
+            ws = I.WORKLOADS["uneven_steps"]
+            cp = I.population(ws, cells=cells, keys=("s", "u", "g", "V0"))
+            cs = {k: torch.as_tensor(cp[k]).cuda() for k in ("s", "g", "u", "V0")}
+
+            def step():  # noqa: F811
+                H.cable_step(plan, cs["s"], cs["g"], cs["u"], cs["V0"], ws.dt, ws.E, 1)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()

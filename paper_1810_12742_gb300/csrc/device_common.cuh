@@ -38,14 +38,17 @@ __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
 }
 
 // ---- reciprocals -------------------------------------------------------------
-// FP64: hardware approximation of the high word, then two Newton steps.
+// FP64: hardware approximation of the high word, then one cubically
+// convergent correction (the series 1/x = r (1 + e + e^2 + ...) with
+// e = 1 - x r, cut after e^2): an approximation good to about 2^-20 leaves a
+// relative error near 2^-60, below FP64 rounding, in three FMAs where two
+// Newton steps take four.  The FP64 pipe bounds the FP64 elimination on
+// this part, so the FMA saved there is time saved.
 __device__ __forceinline__ double rcp_t(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 __device__ __forceinline__ float rcp_t(float x) {
   float r;
