@@ -271,11 +271,60 @@ struct CompMode {
   static constexpr int kTab = kArr > kFac ? kArr : kFac;
   static constexpr int kStageBytes = kTab + 80;
   static constexpr int kStages = 1;
-  static constexpr int kCslot = 0, kCx = 2 * G::kChunk * 16;
-  static constexpr int kCacheBytes = kCx + 2 * G::kChunk * 8;
+  // contiguous blocks (the factor block; d, u, b in the solver layout) are
+  // staged by bulk copies that one lane issues, completing on a per-warp
+  // shared-memory barrier (word kBar of the cache; its phase parity at kBar + 8)
+  static constexpr bool kBulk = true;
+  static constexpr int kCslot = 0, kCx = 2 * G::kChunk * 16, kBar = kCx + 2 * G::kChunk * 8;
+  static constexpr int kCacheBytes = kBar + 16;
   static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes) < 12 ? kSmemPerSm / (kWarps * kWarpBytes) : 12;
   static constexpr bool kWantDs = false;
+  static constexpr int kWaitPolls = 1 << 22;  // bounded wait on a bulk copy (far beyond any real latency)
+  static_assert(kStages == 1 && kBar % 8 == 0 && kStageBytes % 16 == 0, "barrier and buffers aligned");
+
+  __device__ static uint64_t* barrier(unsigned char* buf) {
+    return reinterpret_cast<uint64_t*>(buf + kStageBytes + kBar);
+  }
+  __device__ static bool bulk_staged(int visit) { return kBulk && (visit == 1 || kPk); }
+  // once per warp, before its first task
+  __device__ static void init_warp(unsigned char* wbase, int lane) {
+    if (kBulk && lane == 0) {
+      mbar_init(barrier(wbase));
+      reinterpret_cast<unsigned*>(barrier(wbase) + 1)[0] = 0u;
+    }
+    __syncwarp();
+  }
+  // issue the chunk's bulk copies: one arrival with the expected bytes, then
+  // the copies.  Every lane fences its earlier ordinary accesses first: the
+  // buffer's previous contents, and the factor this warp wrote in the
+  // elimination of the same task, which the substitution's copies read.
+  template <int N>
+  __device__ static void bulk_issue(unsigned char* buf, int lane, unsigned bytes, void* d0, const void* s0,
+                                    void* d1 = nullptr, const void* s1 = nullptr, void* d2 = nullptr,
+                                    const void* s2 = nullptr) {
+    fence_async();
+    __syncwarp();
+    if (lane == 0) {
+      uint64_t* bar = barrier(buf);
+      mbar_expect_tx(bar, N * bytes);
+      if (bytes > 0) {
+        bulk_g2s(d0, s0, bytes, bar);
+        if (N > 1) bulk_g2s(d1, s1, bytes, bar);
+        if (N > 2) bulk_g2s(d2, s2, bytes, bar);
+      }
+    }
+  }
+  // every lane waits for the chunk's bulk copies; a wait that runs out raises
+  // the plan's timeout status and goes on (no access leaves its buffer)
+  __device__ static void bulk_wait(const DevPlan& Pl, unsigned char* buf, int lane) {
+    unsigned* ph = reinterpret_cast<unsigned*>(barrier(buf) + 1);
+    const unsigned parity = *ph;
+    if (!mbar_wait(barrier(buf), parity, kWaitPolls) && Pl.status) atomicCAS(Pl.status, 0, (int)HINES_ERR_TIMEOUT);
+    __syncwarp();
+    if (lane == 0) *ph = parity ^ 1u;
+    __syncwarp();
+  }
 
   __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, Meta<P>& m, int n, int lane,
                                unsigned char* buf, const Prev& pv) {
@@ -283,8 +332,12 @@ struct CompMode {
     build_row_table<P>(m.L, lane, tab);
     const int e = tab[kL];
     if (visit == 1) {
-      stage_block(reinterpret_cast<float4*>(buf), static_cast<const float4*>(Pl.ff4), m.blk, e, lane);
-      cp_commit();
+      if (kBulk) {
+        bulk_issue<1>(buf, lane, (unsigned)e * 16u, buf, static_cast<const float4*>(Pl.ff4) + m.blk);
+      } else {
+        stage_block(reinterpret_cast<float4*>(buf), static_cast<const float4*>(Pl.ff4), m.blk, e, lane);
+        cp_commit();
+      }
       // the parent's solution, unless the predecessor chunk's cache holds it
 #pragma unroll
       for (int h = 0; h < P; ++h) {
@@ -300,6 +353,12 @@ struct CompMode {
     float* sb = su + G::kSlots;
     if (kPk) {
       const long long blk = __shfl_sync(kFull, m.p[0].first, 0);
+      if (kBulk) {
+        // whole 16-byte words: the block's padding (blocks start on multiples
+        // of 4 slots, and the layout's length is one) completes the last
+        bulk_issue<3>(buf, lane, (unsigned)((e + 3) & ~3) * 4u, sd, A.d + blk, su, A.u + blk, sb, A.b + blk);
+        return;
+      }
       stage_block(sd, A.d, blk, e, lane);
       stage_block(su, A.u, blk, e, lane);
       stage_block(sb, A.b, blk, e, lane);
@@ -321,6 +380,7 @@ struct CompMode {
     const int* tab = reinterpret_cast<const int*>(buf + kTab);
     float4* slot = static_cast<float4*>(Pl.cd);
     float2* xlast = static_cast<float2*>(Pl.xlast);
+    if (bulk_staged(visit)) bulk_wait(Pl, buf, lane);
     const int L = m.L;
     if (L == 0) return;
     const int me = P * lane;
@@ -515,6 +575,8 @@ struct FactorMode {
   static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);
   static constexpr bool kWantDs = false;
+  static constexpr bool kBulk = false;
+  __device__ static void init_warp(unsigned char*, int) {}
 
   // Section 1's implicit-Euler system: the membrane part of the diagonal,
   // s (1 + theta dt g), and the right-hand side s (V + dt g (E - (1 - theta) V)),
@@ -807,6 +869,8 @@ struct RefineMode {
   static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);
   static constexpr bool kWantDs = false;
+  static constexpr bool kBulk = false;
+  __device__ static void init_warp(unsigned char*, int) {}
 
   __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, Meta<P>& m, int n, int lane,
                                unsigned char* buf, const Prev& pv) {
@@ -1142,6 +1206,7 @@ __global__ void __launch_bounds__(32 * kWarps, M::kMinBlocks) k_units(DevPlan P,
   extern __shared__ __align__(16) unsigned char smem_u[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* wbase = smem_u + w * M::kWarpBytes;
+  M::init_warp(wbase, lane);
   const int e0 = P.phase_off[phase], ne = P.phase_off[phase + 1] - e0;
   int next = -1;  // a top part handed over to this warp
   for (;;) {
