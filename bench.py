@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--refine-reps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--e2e-pieces", type=int, default=8,
+    ap.add_argument("--e2e-pieces", type=int, default=16,
                     help="cell ranges the end-to-end run pipelines its transfers over")
     ap.add_argument("--shard", action="store_true",
                     help="under torchrun, split the population's cells over the ranks (longest-processing-time "
