@@ -281,11 +281,16 @@ hines_status hines_solve_compensated(hines_plan_t plan, const float *d, const fl
                                      double *x_out, hines_stream_t stream);
 
 /*
- * Mixed-precision solve: elimination in FP32 on FP32 inputs, then
- * refine_steps (0..4) steps of iterative refinement whose residual
- * r = b - A x and correction x += A^{-1} r are carried in FP64 (A and b are
- * the FP32 inputs widened exactly to FP64).  No paper counterpart (Section 2
- * gives the FP64 algorithm only).
+ * Mixed-precision solve: elimination in FP32 on FP32 inputs (the FP32
+ * factor is kept in the plan's workspace), then refine_steps (0..4) steps of
+ * iterative refinement.  A step forms the residual r = b - A x of the
+ * current solution exactly enough for FP64 accuracy without FP64
+ * instructions (products split by FMA into exact pairs, sums compensated),
+ * eliminates it with the stored factor on the same staged chunk, then
+ * substitutes the correction and adds it to x; between steps x is kept as a
+ * double-float pair, the last step writes it in FP64.  A and b are the FP32
+ * inputs taken exactly.  No paper counterpart (Section 2 gives the FP64
+ * algorithm only).
  *   d, u, b      device float[n_unknowns], not modified
  *   x_out        device double[n_unknowns], the solution
  *   cell_relres  device double[n_cells] or NULL: per cell the scaled residual
