@@ -71,3 +71,35 @@ def test_uniform_population_full_size_fp64_every_cell():
     x = torch.as_tensor(pop["b"]).cuda()
     H.solve(plan, torch.as_tensor(pop["d"]).cuda(), torch.as_tensor(pop["u"]).cuda(), x)
     assert per_cell_rel_err(x.cpu().numpy(), _oracle(pop, False), pop["offsets"]).max() <= 1e-12
+
+
+@pytest.mark.parametrize("layout", ["natural", "solver"])
+def test_cable_steps_full_size_every_cell(layout):
+    """Three passive-cable steps (rebuild of d and b from V fused with the FP64
+    solve) on the whole uneven population, then three more re-using the
+    first step's factor (the matrix is constant), each cell against the
+    oracle stepper after 3 and after 6 steps."""
+    w = I.WORKLOADS["uneven_steps"]
+    cp = I.population(w, keys=("s", "a", "u", "g", "V0"))
+    off = cp["offsets"]
+    plan = H.Plan(cp["ncomp"], cp["parent"], reroot=False)
+    cs = {k: torch.as_tensor(cp[k]).cuda() for k in ("s", "g", "u", "V0")}
+    solver = layout == "solver"
+    if solver:
+        s, g, u, V = H.pack(plan, cs["s"]), H.pack(plan, cs["g"]), H.pack_coupling(plan, cs["u"]), H.pack(plan, cs["V0"])
+    else:
+        s, g, u, V = cs["s"], cs["g"], cs["u"], cs["V0"].clone()
+    del cs
+    step = H.cable_step_packed if solver else H.cable_step
+    for _ in range(3):
+        step(plan, s, g, u, V, w.dt, w.E, 1)
+    v3 = (H.unpack(plan, V) if solver else V).cpu().numpy()
+    for _ in range(3):
+        H.cable_step_reuse(plan, s, g, u, V, w.dt, w.E, 1, solver_layout=solver)
+    v6 = (H.unpack(plan, V) if solver else V).cpu().numpy()
+    assert plan.status() == 0
+    del s, g, u, V
+    ref3, _ = oracle.steps_batch(cp["ncomp"], cp["parent"], cp["s"], cp["g"], cp["a"], cp["V0"], 3, w.dt, w.E, 1, NTH)
+    assert per_cell_rel_err(v3, ref3, off).max() <= 1e-12
+    ref6, _ = oracle.steps_batch(cp["ncomp"], cp["parent"], cp["s"], cp["g"], cp["a"], ref3, 3, w.dt, w.E, 1, NTH)
+    assert per_cell_rel_err(v6, ref6, off).max() <= 1e-12
