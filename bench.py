@@ -5,8 +5,9 @@ large, about 228M compartments) from FP32 d, u, b to an FP64 solution x with
 the compensated FP32 elimination (hines_solve_compensated: double-float
 arithmetic built from FP32 error-free transformations, no FP64 instruction),
 inputs resident in HBM.  The same batch is also solved in plain FP64
-(hines_solve) and with FP32 elimination + FP64 residual refinement
-(hines_solve_refine) for the comparison the metric asks for; each result is
+(hines_solve) and with FP32 elimination + iterative refinement whose
+residual is formed to FP64 accuracy from error-free FP32 products
+(hines_solve_refine), for the comparison the metric asks for; each result is
 checked against the oracle on sampled cells.  The inputs (2.7 GB FP32 plus
 the 1.8 GB solution) exceed L2, so no flush is needed.
 

@@ -385,7 +385,9 @@ def cable_solve_packed(plan: Plan, s, g, u, y, dt: float, theta: int = 1):
 
 
 def solve_refine(plan: Plan, d, u, b, x=None, steps: int = 2, relres=None):
-    """FP32 elimination + FP64 residual/correction refinement; returns x (float64)."""
+    """FP32 elimination + iterative refinement (residual to FP64 accuracy from
+    error-free FP32 products, fused with the correction's elimination);
+    returns x (float64)."""
     torch = _torch()
     n = plan.n_unknowns
     if x is None:
