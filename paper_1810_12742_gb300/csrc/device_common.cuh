@@ -10,10 +10,6 @@ namespace hines {
 namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kSlots = 1024;  // 32 lanes x 32 steps
-
-__device__ __forceinline__ int sidx(int k, int j) { return (k << 5) + (j ^ (k & 31)); }
-
 // ---- asynchronous global -> shared copies (LDGSTS) --------------------------
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -111,46 +107,6 @@ __device__ __forceinline__ ff ff_sub(ff x, float yh, float yl) {
   const float e = __fadd_rn(__fsub_rn(x.h, __fsub_rn(s, bb)), __fsub_rn(-yh, bb));
   return ff_renorm(s, __fadd_rn(e, __fsub_rn(x.l, yl)));
 }
-// x - (yh + yl) when |x| >= |yh| (the diagonal chain of a diagonally dominant
-// matrix: d_{i-1} > u_i^2 / d'_i), fast two-sum on the leading parts
-__device__ __forceinline__ ff ff_sub_dom(float x, float yh, float yl) {
-  const float s = __fsub_rn(x, yh);
-  const float e = __fsub_rn(__fsub_rn(x, s), yh);
-  return ff_renorm(s, __fsub_rn(e, yl));
-}
-// f = u / d for an FP32 u
-__device__ __forceinline__ ff ff_div_f(float u, ff d) {
-  const float r = rcp_t(d.h);
-  const float F = __fmul_rn(u, r);
-  float t = fmaf(-F, d.h, u);
-  t = fmaf(-F, d.l, t);
-  return ff_renorm(F, __fmul_rn(t, r));
-}
-// n / d
-__device__ __forceinline__ ff ff_div(ff n, ff d) {
-  const float r = rcp_t(d.h);
-  const float X = __fmul_rn(n.h, r);
-  float t = fmaf(-X, d.h, n.h);
-  t = __fadd_rn(t, n.l);
-  t = fmaf(-X, d.l, t);
-  return ff_renorm(X, __fmul_rn(t, r));
-}
-// f * u for an FP32 u (exact leading product plus the lo term)
-__device__ __forceinline__ ff ff_mul_f(ff f, float u) {
-  const float P = __fmul_rn(f.h, u);
-  float p = fmaf(f.h, u, -P);
-  p = fmaf(f.l, u, p);
-  return {P, p};
-}
-// f * b
-__device__ __forceinline__ ff ff_mul(ff f, ff b) {
-  const float Q = __fmul_rn(f.h, b.h);
-  float q = fmaf(f.h, b.h, -Q);
-  q = fmaf(f.h, b.l, q);
-  q = fmaf(f.l, b.h, q);
-  return {Q, q};
-}
-
 // ---- one or two independent values per thread -------------------------------
 // The solve kernels give a lane one or two branch pieces.  Their arithmetic is
 // written once over a value type V: float for one piece, F2 for two, whose

@@ -114,10 +114,10 @@ hines_status upload(hines_plan_t p) {
   // the factor is indexed by natural or solver-layout position
   const size_t fac_b = align256(std::max(n, (size_t)H.n_packed) * 8 + 8), cd_b = align256(nb * 16 + 16),
                cb_b = align256(nb * 32 + 32),
-               ds_b = align256(nb * 16 + 16), xl_b = align256(nb * 8 + 8), red_b = align256(nc * 8 + 8),
+               xl_b = align256(nb * 8 + 8), red_b = align256(nc * 8 + 8),
                cnt_b = align256((nc + 4) * 4), rw_b = align256(std::max(n, (size_t)H.n_packed) * 4 + 4),
                ff4_b = align256((size_t)H.n_packed * 16 + 16);
-  const size_t wtotal = fac_b + cd_b + cb_b + ds_b + xl_b + red_b + cnt_b + rw_b + ff4_b;
+  const size_t wtotal = fac_b + cd_b + cb_b + xl_b + red_b + cnt_b + rw_b + ff4_b;
   if (cudaMalloc(&p->work, wtotal) != cudaSuccess) {
     cudaGetLastError();
     p->work = nullptr;
@@ -131,8 +131,6 @@ hines_status upload(hines_plan_t p) {
   w += cd_b;
   D.cb = w;
   w += cb_b;
-  D.dstate = w;
-  w += ds_b;
   D.xlast = w;
   w += xl_b;
   D.red = w;

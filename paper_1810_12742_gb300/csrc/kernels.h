@@ -61,7 +61,6 @@ struct DevPlan {
                           // arrays (refine)
   void* cd = nullptr;     // n_branches * 16 bytes: child-to-parent contribution (or root solution) per position
   void* cb = nullptr;     // n_branches * 32 bytes: per-branch reductions of the refinement
-  void* dstate = nullptr; // n_branches * 16 bytes: folded distal state per position (compensated)
   void* xlast = nullptr;  // n_branches * 8 bytes: solution at the distal compartment per position
   void* red = nullptr;    // n_cells * 8 bytes: per-cell reductions
   void* rw = nullptr;     // 4 bytes per natural or solver-layout slot: the refinement's eliminated residual

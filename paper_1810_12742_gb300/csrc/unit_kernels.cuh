@@ -95,7 +95,6 @@ template <int P>
 struct Meta {
   long long blk;  // the chunk's block offset in the solver layout
   Piece p[P];
-  float4 ds[P];  // compensated substitution: folded distal state left by the elimination
   // substitution: the parent's solution when another chunk than the cached
   // predecessor left it, fetched while the chunk is staged so that its
   // latency overlaps the staging copies
@@ -104,7 +103,7 @@ struct Meta {
 };
 
 template <bool kPk, int P>
-__device__ __forceinline__ Meta<P> load_meta(const DevPlan& Pl, int c0, int n, int lane, bool active, bool want_ds,
+__device__ __forceinline__ Meta<P> load_meta(const DevPlan& Pl, int c0, int n, int lane, bool active,
                                              bool want_blk = false) {
   Meta<P> m;
   m.blk = 0;
@@ -113,11 +112,9 @@ __device__ __forceinline__ Meta<P> load_meta(const DevPlan& Pl, int c0, int n, i
   for (int h = 0; h < P; ++h) {
     const int i = P * lane + h;
     Piece q{0, -1, -1, 0, 0, 0, 0, 0};
-    m.ds[h] = make_float4(0.f, 0.f, 0.f, 0.f);
     m.xpre[h].d = 0.0;
     if (active && i < n) {
       const int pos = c0 + i;
-      if (want_ds) m.ds[h] = static_cast<const float4*>(Pl.dstate)[pos];
       const BrMetaT t = Pl.tmeta[pos];
       if (kPk) {
         const longlong2 w = Pl.pk_meta[pos];
@@ -279,7 +276,6 @@ struct CompMode {
   static constexpr int kCacheBytes = kBar + 16;
   static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes) < 12 ? kSmemPerSm / (kWarps * kWarpBytes) : 12;
-  static constexpr bool kWantDs = false;
   static constexpr int kWaitPolls = 1 << 22;  // bounded wait on a bulk copy (far beyond any real latency)
   static_assert(kStages == 1 && kBar % 8 == 0 && kStageBytes % 16 == 0, "barrier and buffers aligned");
 
@@ -574,7 +570,6 @@ struct FactorMode {
   static constexpr int kCacheBytes = kCx + 2 * G::kChunk * (int)sizeof(T);
   static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);
-  static constexpr bool kWantDs = false;
   static constexpr bool kBulk = false;
   __device__ static void init_warp(unsigned char*, int) {}
 
@@ -868,7 +863,6 @@ struct RefineMode {
   static constexpr int kCacheBytes = kCx + 2 * G::kChunk * 8;
   static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);
-  static constexpr bool kWantDs = false;
   static constexpr bool kBulk = false;
   __device__ static void init_warp(unsigned char*, int) {}
 
@@ -1131,7 +1125,7 @@ __device__ void run_task(const DevPlan& Pl, const typename M::Args& A, int t, in
   unsigned char* cache = wbase + M::kStages * M::kStageBytes;
   auto buf = [wbase](int which) { return wbase + (M::kStages == 2 ? which : 0) * M::kStageBytes; };
   auto meta = [&](const Pos& p) {
-    return load_meta<M::kPacked, P>(Pl, p.c0, p.n, lane, p.visit < ve, M::kWantDs && p.visit == 1, M::kNeedsBlk);
+    return load_meta<M::kPacked, P>(Pl, p.c0, p.n, lane, p.visit < ve, M::kNeedsBlk);
   };
   // metadata runs two chunks ahead; with two staging buffers the next chunk
   // is staged while this one is computed, with one right after this one's
