@@ -714,10 +714,10 @@ def main():
                                 "correction-elimination pass and a correction-substitution pass"},
         "e2e": {"value": n_job / (e2e_ms * 1e-3), "unit": "compartments/s",
                 "h2d_bytes_per_step": 12 * n_job, "d2h_bytes_per_step": 8 * n_job, "max_rel_err": e2e_err,
-                "path": f"Python hines.HostPipeline.solve_compensated: pinned host arrays, cut into "
-                        f"{args.e2e_pieces} pieces of consecutive cells; torch copies on three streams overlap "
-                        "each piece's host-to-device copy, its C-ABI device solve (hines_solve_compensated) and "
-                        "its device-to-host copy"},
+                "path": f"C-ABI hines_pipeline_solve_compensated (through hines.HostPipeline) on pinned host "
+                        f"arrays: the batch cut into {args.e2e_pieces} runs of consecutive cells, each with its own "
+                        "plan; per run the host-to-device copies, the device solve and the device-to-host copy on "
+                        "three internal streams, overlapped"},
         "clocks": clk.summary(),
         "gpu_launches": 2 * args.steps,
     }

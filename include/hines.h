@@ -426,6 +426,53 @@ hines_status hines_solve_f64_noalloc(int64_t n_unknowns, int32_t n_cells, const 
 /* Read (synchronously) and clear the plan's device status word. */
 hines_status hines_plan_status(hines_plan_t plan, int32_t *status_out);
 
+/*
+ * Host pipeline: hines_solve_compensated from arrays in host memory, with
+ * the host-device transfers overlapped with the solve.  No paper
+ * counterpart.  Creation cuts the batch into `pieces` runs of consecutive
+ * cells of about equal compartment counts (fewer where cells are few or
+ * large), builds one plan per run (opts as for hines_plan_create; host_only
+ * is rejected) and allocates the runs' device copies of d, u, b and x on the
+ * current device (the pipeline owns them; hines_pipeline_destroy releases
+ * everything, after its streams are idle).
+ *   out       receives the pipeline, NULL on failure
+ *   n_cells, ncomp, parent   as for hines_plan_create (host arrays)
+ *   pieces    >= 1
+ * Errors: those of hines_plan_create, HINES_ERR_OOM for the buffers,
+ * HINES_ERR_CUDA for streams or events.
+ */
+typedef struct hines_pipeline_s *hines_pipeline_t;
+hines_status hines_pipeline_create(hines_pipeline_t *out, int32_t n_cells, const int32_t *ncomp,
+                                   const int32_t *parent, int32_t pieces, const hines_plan_opts *opts);
+
+/* The number of runs the batch was cut into, and the batch's compartments. */
+hines_status hines_pipeline_info(hines_pipeline_t pipeline, int32_t *pieces, int64_t *n_unknowns);
+
+/*
+ * The compensated solve of the whole batch from host arrays (natural layout
+ * of the batch, as for hines_solve_compensated):
+ *   d, u, b   host float[n_unknowns], not modified
+ *   x_out     host double[n_unknowns], the solution
+ * Per run: the three input copies on one internal stream, the device solve
+ * on a second, the copy of x back on a third, joined by events; the work is
+ * ordered after everything enqueued on `stream` before the call, and
+ * `stream` waits for all of it (x_out is complete when the stream reaches
+ * that point).  The transfers overlap only when the host arrays are
+ * page-locked (cudaHostAlloc, cudaHostRegister, pinned torch tensors); with
+ * pageable memory the copies still complete, without overlap.  Calls on one
+ * pipeline must be ordered on one stream (they share its buffers).  Results
+ * are those of hines_solve_compensated on each run's plan.
+ * Errors: HINES_ERR_INVALID_ARG (null pipeline or array), HINES_ERR_DEVICE
+ * (another device current than at creation), HINES_ERR_CUDA.
+ */
+hines_status hines_pipeline_solve_compensated(hines_pipeline_t pipeline, const float *d, const float *u,
+                                              const float *b, double *x_out, hines_stream_t stream);
+
+/* Read (synchronously) and clear the runs' plan status words; the largest. */
+hines_status hines_pipeline_status(hines_pipeline_t pipeline, int32_t *status_out);
+
+hines_status hines_pipeline_destroy(hines_pipeline_t pipeline);
+
 /* Static text of a status code. */
 const char *hines_status_string(int32_t status);
 

@@ -38,6 +38,8 @@ EXPORTS = [
     "hines_plan_export_packed", "hines_pack", "hines_unpack", "hines_solve_packed", "hines_solve_compensated_packed",
     "hines_cable_step_packed", "hines_cable_solve_packed", "hines_cable_step_reuse",
     "hines_pack_coupling", "hines_plan_export_reroot",
+    "hines_pipeline_create", "hines_pipeline_info", "hines_pipeline_solve_compensated", "hines_pipeline_status",
+    "hines_pipeline_destroy",
 ]
 
 
@@ -98,6 +100,11 @@ def lib():
             L.hines_cable_solve_packed.argtypes = [vp, vp, vp, vp, vp, f64, i32, vp]
             L.hines_cable_step_reuse.argtypes = [vp, vp, vp, vp, vp, f64, f64, i32, i32, vp]
             L.hines_status_string.argtypes = [i32]
+            L.hines_pipeline_create.argtypes = [vp, i32, vp, vp, i32, vp]
+            L.hines_pipeline_info.argtypes = [vp, vp, vp]
+            L.hines_pipeline_solve_compensated.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.hines_pipeline_status.argtypes = [vp, vp]
+            L.hines_pipeline_destroy.argtypes = [vp]
             L.hines_status_string.restype = ctypes.c_char_p
             for name in EXPORTS:
                 if name != "hines_status_string":
@@ -451,92 +458,67 @@ def cable_loss_seed(plan: Plan, V, target, vbar):
                                        _dptr(vbar, f, n, "vbar"), _stream()), "hines_cable_loss_seed")
 
 
-def _host_staging(plan: Plan):
-    """Device staging buffers (d, u, b in FP32, x in FP64) owned by the plan object."""
-    torch = _torch()
-    st = getattr(plan, "_staging", None)
-    if st is None:
-        n = plan.n_unknowns
-        st = tuple(torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)) + (
-            torch.empty(n, dtype=torch.float64, device="cuda"),)
-        plan._staging = st
-    return st
-
-
-def solve_refine_host(plan: Plan, d, u, b, x, steps: int = 2):
-    """solve_refine on host tensors (pinned for asynchronous copies): copies d,
-    u, b to device staging buffers owned by the plan object, solves, and copies
-    x back, all on the current stream."""
-    st = _host_staging(plan)
-    for dst, src in zip(st[:3], (d, u, b)):
-        dst.copy_(src, non_blocking=True)
-    solve_refine(plan, st[0], st[1], st[2], st[3], steps)
-    x.copy_(st[3], non_blocking=True)
-    return x
-
-
-def solve_compensated_host(plan: Plan, d, u, b, x):
-    """solve_compensated on host tensors (pinned for asynchronous copies), with
-    the same staging as solve_refine_host."""
-    st = _host_staging(plan)
-    for dst, src in zip(st[:3], (d, u, b)):
-        dst.copy_(src, non_blocking=True)
-    solve_compensated(plan, st[0], st[1], st[2], st[3])
-    x.copy_(st[3], non_blocking=True)
-    return x
-
-
 class HostPipeline:
-    """The compensated solve from host arrays, with the transfers overlapped:
-    the batch is cut into ``pieces`` runs of consecutive cells of about equal
-    size, each with its own plan and device buffers, and per piece the
-    host-to-device copy, the solve and the device-to-host copy run on three
-    streams, so that piece k is solved while piece k+1 arrives and piece k-1
-    leaves.  ``solve_compensated`` takes pinned host tensors in the natural
-    layout of the whole batch and returns when the work is enqueued on the
-    current stream (which waits for all of it).  plan_options go to every
-    piece's plan."""
+    """hines_pipeline_*: the compensated solve from host arrays, with the
+    transfers overlapped.  The library cuts the batch into ``pieces`` runs of
+    consecutive cells of about equal size, each with its own plan and device
+    buffers, and per run overlaps the host-to-device copies, the solve and the
+    copy back on three internal streams.  ``solve_compensated`` takes CPU
+    tensors in the natural layout of the whole batch (pinned, for the
+    overlap) and enqueues the work after the current stream, which then waits
+    for all of it.  plan_options go to every run's plan."""
 
     def __init__(self, ncomp, parent, pieces: int = 8, **plan_options):
-        torch = _torch()
-        nc = np.ascontiguousarray(ncomp, np.int64)
+        self._h = ctypes.c_void_p()
+        nc = np.ascontiguousarray(ncomp, np.int32)
         pa = np.ascontiguousarray(parent, np.int32)
-        off = np.concatenate(([0], np.cumsum(nc)))
-        total = int(off[-1])
-        pieces = max(1, min(int(pieces), nc.size))
-        # cell boundaries closest to equal compartment counts
-        cuts = np.searchsorted(off, np.linspace(0, total, pieces + 1)[1:-1], side="left")
-        bounds = np.unique(np.concatenate(([0], cuts, [nc.size])))
-        self.parts = []
-        for c0, c1 in zip(bounds[:-1], bounds[1:]):
-            lo, hi = int(off[c0]), int(off[c1])
-            plan = Plan(nc[c0:c1], pa[lo:hi], **plan_options)
-            n = hi - lo
-            bufs = tuple(torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)) + (
-                torch.empty(n, dtype=torch.float64, device="cuda"),)
-            self.parts.append((lo, hi, plan, bufs))
-        self.n_unknowns = total
-        self.streams = [torch.cuda.Stream() for _ in range(3)]
+        o = dict(host_only=False, split_branches=0, pieces_per_lane=0, sort_by_length=False, pack_compartments=0,
+                 reroot=False, even_cuts=False, pack_whole=0)
+        unknown = set(plan_options) - set(o)
+        if unknown:
+            raise TypeError(f"unknown plan options: {sorted(unknown)}")
+        o.update(plan_options)
+        opts = PlanOpts(int(o["host_only"]), int(o["split_branches"]), int(o["pieces_per_lane"]),
+                        int(o["sort_by_length"]), int(o["pack_compartments"]), int(o["reroot"]),
+                        int(o["even_cuts"]), int(o["pack_whole"]))
+        _check(lib().hines_pipeline_create(ctypes.byref(self._h), nc.size, _np_ptr(nc), _np_ptr(pa), int(pieces),
+                                           ctypes.byref(opts)), "hines_pipeline_create")
+        npieces, n = ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().hines_pipeline_info(self._h, ctypes.byref(npieces), ctypes.byref(n)), "hines_pipeline_info")
+        self.pieces, self.n_unknowns = npieces.value, n.value
 
     def solve_compensated(self, d, u, b, x):
         torch = _torch()
-        cur = torch.cuda.current_stream()
-        s_in, s_run, s_out = self.streams
-        for s in self.streams:
-            s.wait_stream(cur)
-        for lo, hi, plan, (dd, uu, bb, xx) in self.parts:
-            with torch.cuda.stream(s_in):
-                for dst, src in zip((dd, uu, bb), (d, u, b)):
-                    dst.copy_(src[lo:hi], non_blocking=True)
-                ready = torch.cuda.Event()
-                ready.record(s_in)
-            with torch.cuda.stream(s_run):
-                s_run.wait_event(ready)
-                solve_compensated(plan, dd, uu, bb, xx)
-                done = torch.cuda.Event()
-                done.record(s_run)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(done)
-                x[lo:hi].copy_(xx, non_blocking=True)
-        cur.wait_stream(s_out)
+        n = self.n_unknowns
+        _check(lib().hines_pipeline_solve_compensated(self._h, _hptr(d, torch.float32, n, "d"),
+                                                      _hptr(u, torch.float32, n, "u"),
+                                                      _hptr(b, torch.float32, n, "b"),
+                                                      _hptr(x, torch.float64, n, "x"), _stream()),
+               "hines_pipeline_solve_compensated")
         return x
+
+    def status(self) -> int:
+        s = ctypes.c_int32()
+        _check(lib().hines_pipeline_status(self._h, ctypes.byref(s)), "hines_pipeline_status")
+        return s.value
+
+    def close(self):
+        if self._h:
+            lib().hines_pipeline_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _hptr(t, dtype, n, name):
+    """Pointer to a contiguous CPU tensor (host memory)."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name}: expected a CPU tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name}: expected contiguous {dtype} with {n} elements, got {t.dtype} {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())

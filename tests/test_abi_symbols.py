@@ -68,3 +68,25 @@ def test_argument_errors_without_gpu():
     two = H.Plan(nc, pa, host_only=True, pieces_per_lane=2)
     assert two.export_packed().tolist() == [1, -1, 0, -1]
     assert L.hines_plan_destroy(None) == H.HINES_OK
+
+
+def test_pipeline_argument_errors_without_gpu():
+    L = H.lib()
+    h = ctypes.c_void_p()
+    nc = np.array([2], np.int32)
+    pa = np.array([-1, 0], np.int32)
+    ncp, pap = nc.ctypes.data_as(ctypes.c_void_p), pa.ctypes.data_as(ctypes.c_void_p)
+    assert L.hines_pipeline_create(None, 1, ncp, pap, 2, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_pipeline_create(ctypes.byref(h), 1, ncp, pap, 0, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_pipeline_create(ctypes.byref(h), -1, ncp, pap, 2, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_pipeline_create(ctypes.byref(h), 1, None, pap, 2, None) == H.HINES_ERR_INVALID_ARG
+    opts = H.PlanOpts(1)  # a pipeline solves: host-only plans are refused
+    assert L.hines_pipeline_create(ctypes.byref(h), 1, ncp, pap, 2, ctypes.byref(opts)) == H.HINES_ERR_INVALID_ARG
+    bad = np.array([-3], np.int32)
+    assert L.hines_pipeline_create(ctypes.byref(h), 1, bad.ctypes.data_as(ctypes.c_void_p), pap, 2,
+                                   None) == H.HINES_ERR_INVALID_ARG
+    assert not h.value
+    assert L.hines_pipeline_info(None, None, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_pipeline_solve_compensated(None, None, None, None, None, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_pipeline_status(None, None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_pipeline_destroy(None) == H.HINES_OK

@@ -139,3 +139,13 @@ def test_host_pipeline_equals_device_solve():
             assert np.array_equal(got, x)  # one piece: the same plan, the same arithmetic
         assert cell_rel_err(got, x, plan.offsets).max() <= 1e-12
         assert cell_rel_err(got, ref, plan.offsets).max() <= 1e-10
+        assert pipe.status() == 0
+    # pageable host arrays: the copies complete without overlap, same results
+    pipe = H.HostPipeline(pop["ncomp"], pop["parent"], pieces=3)
+    xp = torch.zeros(plan.n_unknowns, dtype=torch.float64)
+    pipe.solve_compensated(*(torch.as_tensor(f32[k]) for k in ("d", "u", "b")), xp)
+    torch.cuda.synchronize()
+    pipe.solve_compensated(host["d"], host["u"], host["b"], xh)
+    torch.cuda.synchronize()
+    assert np.array_equal(xp.numpy(), xh.numpy())
+    pipe.close()
