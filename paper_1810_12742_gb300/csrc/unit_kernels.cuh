@@ -576,7 +576,12 @@ struct FactorMode {
   // Section 1's implicit-Euler system: the membrane part of the diagonal,
   // s (1 + theta dt g), and the right-hand side s (V + dt g (E - (1 - theta) V)),
   // each in the fewest operations (theta = 1: s (V + dt E g))
-  __device__ static T cable_diag(const Args& A, T si, T gi) { return si * fma(A.theta * A.dt, gi, T(1)); }
+  // the diagonal less the compartment's own edge to its parent, s (1 + theta
+  // dt g) - a_own, in one FMA (a cell's root, which has no such edge, adds
+  // its u back: the same operations in both layouts)
+  __device__ static T cable_diag_edge(const Args& A, T si, T gi, T ui) {
+    return fma(si, fma(A.theta * A.dt, gi, T(1)), -ui);
+  }
   __device__ static T cable_rhs(const Args& A, T si, T gi, T vi) {
     if (A.theta == T(1)) return si * fma(A.dt * A.E, gi, vi);
     return si * fma(A.dt * gi, fma(A.theta - T(1), vi, A.E), vi);
@@ -605,8 +610,8 @@ struct FactorMode {
       const long long blk = __shfl_sync(kFull, m.p[0].first, 0);
       const int e = tab[kL];
       if (kCable && visit == 0) {
-        // the block's rows in place; the own edge to the parent is taken off
-        // the diagonal in compute(), where the cell's root compartment is known
+        // the block's rows in place; every diagonal loses its own edge here,
+        // and compute() gives it back to a cell's root compartment (known there)
         if (kReuse) {  // the stored factor; only the right-hand side is rebuilt
           stage_block(sd, fac, blk, e, lane);
           stage_block(su, A.u, blk, e, lane);
@@ -618,7 +623,7 @@ struct FactorMode {
             sb[i] = A.rhs_from_V ? cable_rhs(A, A.s[g], A.g[g], vi) : vi;
           } else {
             const T si = A.s[g], gi = A.g[g], ui = A.u[g];
-            sd[i] = cable_diag(A, si, gi);
+            sd[i] = cable_diag_edge(A, si, gi, ui);
             su[i] = ui;
             sb[i] = A.rhs_from_V ? cable_rhs(A, si, gi, vi) : vi;
           }
@@ -652,8 +657,8 @@ struct FactorMode {
       // the own edge to the parent comes off every diagonal but a cell root's
       for_chunk_elements(m, n, lane, [&](int i, int t, int row, long long g, bool root) {
         const T si = A.s[g], gi = A.g[g], ui = A.u[g], vi = A.x[g];
-        T dd = cable_diag(A, si, gi);
-        if (!(root && t == 0)) dd -= ui;  // own edge to the parent
+        T dd = cable_diag_edge(A, si, gi, ui);
+        if (root && t == 0) dd += ui;  // a cell's root: no edge to a parent
         const int q = nidx<P>(row, i);
         sd[q] = dd;
         su[q] = ui;
@@ -680,18 +685,13 @@ struct FactorMode {
     for (int h = 0; h < P; ++h) first_row[h] = m.p[h].len > 0 ? L - m.p[h].len : kL;
     if (visit == 0) {
       if (kPk && kCable && !kReuse) {
-        // solver layout: own edge to the parent, except at a cell's root
-        // compartment (the proximal compartment of a root piece, row L - 1)
+        // solver layout: a cell's root compartment (the proximal compartment
+        // of a root piece, row L - 1) gets back the edge staging took off
 #pragma unroll
-        for (int r = 0; r < kL; ++r) {
-          if (r < L) {
-#pragma unroll
-            for (int h = 0; h < P; ++h) {
-              if (r >= first_row[h] && !(m.p[h].pcomp < 0 && r == L - 1)) {
-                const int i = rows.slot(r, me + h);
-                sd[i] -= su[i];
-              }
-            }
+        for (int h = 0; h < P; ++h) {
+          if (m.p[h].len > 0 && m.p[h].pcomp < 0) {
+            const int i = rows.slot(L - 1, me + h);
+            sd[i] += su[i];
           }
         }
       }
