@@ -237,6 +237,57 @@ __device__ __forceinline__ typename VOf<P>::type vpack(const float* a) {
 // the second half of v replaced by w (the shorter piece joins its chain)
 __device__ __forceinline__ F2 vset_hi(F2 v, float w) { return f2_make(f2_lo(v), w); }
 
+// ---- bulk staging -------------------------------------------------------------
+// Contiguous blocks are staged by one-dimensional bulk copies that one lane
+// issues, completing on a per-warp shared-memory barrier at byte kOff of the
+// warp's region (its phase parity in the word after it).  A mode with one
+// staging buffer has at most one staging in flight, so one barrier does.
+template <int kOff>
+struct BulkStage {
+  static_assert(kOff % 8 == 0, "barrier alignment");
+  static constexpr int kBytes = 16;           // barrier + parity word
+  static constexpr int kWaitPolls = 1 << 22;  // bounded wait (far beyond any real latency)
+  __device__ static uint64_t* barrier(unsigned char* wbase) { return reinterpret_cast<uint64_t*>(wbase + kOff); }
+  // once per warp, before its first task
+  __device__ static void init(unsigned char* wbase, int lane) {
+    if (lane == 0) {
+      mbar_init(barrier(wbase));
+      reinterpret_cast<unsigned*>(barrier(wbase) + 1)[0] = 0u;
+    }
+    __syncwarp();
+  }
+  // one arrival with the expected bytes, then the copies.  Every lane fences
+  // its earlier ordinary accesses first: the buffer's previous contents, and
+  // factors this warp wrote in an earlier chunk of the same task, which the
+  // copies may read.
+  template <int N>
+  __device__ static void issue(unsigned char* wbase, int lane, unsigned bytes, void* d0, const void* s0,
+                               void* d1 = nullptr, const void* s1 = nullptr, void* d2 = nullptr,
+                               const void* s2 = nullptr) {
+    fence_async();
+    __syncwarp();
+    if (lane == 0) {
+      uint64_t* bar = barrier(wbase);
+      mbar_expect_tx(bar, N * bytes);
+      if (bytes > 0) {
+        bulk_g2s(d0, s0, bytes, bar);
+        if (N > 1) bulk_g2s(d1, s1, bytes, bar);
+        if (N > 2) bulk_g2s(d2, s2, bytes, bar);
+      }
+    }
+  }
+  // every lane waits for the staged copies; a wait that runs out raises the
+  // plan's timeout status and goes on (no access leaves its buffer)
+  __device__ static void wait(const DevPlan& Pl, unsigned char* wbase, int lane) {
+    unsigned* ph = reinterpret_cast<unsigned*>(barrier(wbase) + 1);
+    const unsigned parity = *ph;
+    if (!mbar_wait(barrier(wbase), parity, kWaitPolls) && Pl.status) atomicCAS(Pl.status, 0, (int)HINES_ERR_TIMEOUT);
+    __syncwarp();
+    if (lane == 0) *ph = parity ^ 1u;
+    __syncwarp();
+  }
+};
+
 // ============================================================================
 // Compensated mode: FP32 inputs, double-float arithmetic from FP32 error-free
 // transformations, FP64 solution.  The elimination leaves, per compartment k,
@@ -269,57 +320,18 @@ struct CompMode {
   static constexpr int kStageBytes = kTab + 80;
   static constexpr int kStages = 1;
   // contiguous blocks (the factor block; d, u, b in the solver layout) are
-  // staged by bulk copies that one lane issues, completing on a per-warp
-  // shared-memory barrier (word kBar of the cache; its phase parity at kBar + 8)
+  // staged by bulk copies (BulkStage, its barrier after the caches)
   static constexpr bool kBulk = true;
   static constexpr int kCslot = 0, kCx = 2 * G::kChunk * 16, kBar = kCx + 2 * G::kChunk * 8;
   static constexpr int kCacheBytes = kBar + 16;
   static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes) < 12 ? kSmemPerSm / (kWarps * kWarpBytes) : 12;
-  static constexpr int kWaitPolls = 1 << 22;  // bounded wait on a bulk copy (far beyond any real latency)
-  static_assert(kStages == 1 && kBar % 8 == 0 && kStageBytes % 16 == 0, "barrier and buffers aligned");
+  static_assert(kStages == 1 && kStageBytes % 16 == 0, "one staging buffer, 16-byte aligned");
+  using Bulk = BulkStage<kStageBytes + kBar>;
 
-  __device__ static uint64_t* barrier(unsigned char* buf) {
-    return reinterpret_cast<uint64_t*>(buf + kStageBytes + kBar);
-  }
   __device__ static bool bulk_staged(int visit) { return kBulk && (visit == 1 || kPk); }
-  // once per warp, before its first task
   __device__ static void init_warp(unsigned char* wbase, int lane) {
-    if (kBulk && lane == 0) {
-      mbar_init(barrier(wbase));
-      reinterpret_cast<unsigned*>(barrier(wbase) + 1)[0] = 0u;
-    }
-    __syncwarp();
-  }
-  // issue the chunk's bulk copies: one arrival with the expected bytes, then
-  // the copies.  Every lane fences its earlier ordinary accesses first: the
-  // buffer's previous contents, and the factor this warp wrote in the
-  // elimination of the same task, which the substitution's copies read.
-  template <int N>
-  __device__ static void bulk_issue(unsigned char* buf, int lane, unsigned bytes, void* d0, const void* s0,
-                                    void* d1 = nullptr, const void* s1 = nullptr, void* d2 = nullptr,
-                                    const void* s2 = nullptr) {
-    fence_async();
-    __syncwarp();
-    if (lane == 0) {
-      uint64_t* bar = barrier(buf);
-      mbar_expect_tx(bar, N * bytes);
-      if (bytes > 0) {
-        bulk_g2s(d0, s0, bytes, bar);
-        if (N > 1) bulk_g2s(d1, s1, bytes, bar);
-        if (N > 2) bulk_g2s(d2, s2, bytes, bar);
-      }
-    }
-  }
-  // every lane waits for the chunk's bulk copies; a wait that runs out raises
-  // the plan's timeout status and goes on (no access leaves its buffer)
-  __device__ static void bulk_wait(const DevPlan& Pl, unsigned char* buf, int lane) {
-    unsigned* ph = reinterpret_cast<unsigned*>(barrier(buf) + 1);
-    const unsigned parity = *ph;
-    if (!mbar_wait(barrier(buf), parity, kWaitPolls) && Pl.status) atomicCAS(Pl.status, 0, (int)HINES_ERR_TIMEOUT);
-    __syncwarp();
-    if (lane == 0) *ph = parity ^ 1u;
-    __syncwarp();
+    if (kBulk) Bulk::init(wbase, lane);
   }
 
   __device__ static void stage(const DevPlan& Pl, const Args& A, int visit, Meta<P>& m, int n, int lane,
@@ -329,7 +341,7 @@ struct CompMode {
     const int e = tab[kL];
     if (visit == 1) {
       if (kBulk) {
-        bulk_issue<1>(buf, lane, (unsigned)e * 16u, buf, static_cast<const float4*>(Pl.ff4) + m.blk);
+        Bulk::template issue<1>(buf, lane, (unsigned)e * 16u, buf, static_cast<const float4*>(Pl.ff4) + m.blk);
       } else {
         stage_block(reinterpret_cast<float4*>(buf), static_cast<const float4*>(Pl.ff4), m.blk, e, lane);
         cp_commit();
@@ -352,7 +364,8 @@ struct CompMode {
       if (kBulk) {
         // whole 16-byte words: the block's padding (blocks start on multiples
         // of 4 slots, and the layout's length is one) completes the last
-        bulk_issue<3>(buf, lane, (unsigned)((e + 3) & ~3) * 4u, sd, A.d + blk, su, A.u + blk, sb, A.b + blk);
+        Bulk::template issue<3>(buf, lane, (unsigned)((e + 3) & ~3) * 4u, sd, A.d + blk, su, A.u + blk, sb,
+                                A.b + blk);
         return;
       }
       stage_block(sd, A.d, blk, e, lane);
@@ -376,7 +389,7 @@ struct CompMode {
     const int* tab = reinterpret_cast<const int*>(buf + kTab);
     float4* slot = static_cast<float4*>(Pl.cd);
     float2* xlast = static_cast<float2*>(Pl.xlast);
-    if (bulk_staged(visit)) bulk_wait(Pl, buf, lane);
+    if (bulk_staged(visit)) Bulk::wait(Pl, buf, lane);
     const int L = m.L;
     if (L == 0) return;
     const int me = P * lane;
@@ -521,9 +534,14 @@ struct CompMode {
 };
 
 // ============================================================================
-// Factor mode (FP64, FP32, passive cable): the elimination writes the
-// reciprocal eliminated diagonal to the workspace and the eliminated
-// right-hand side in place; the substitution reads them back.  In cable mode
+// Factor mode (FP64, FP32, passive cable): the elimination leaves, per
+// compartment, the reciprocal eliminated diagonal and the eliminated
+// right-hand side; the substitution reads them back.  FP64 writes the pair
+// as 16 bytes into the plan's factor block, in the chunk's block order of the
+// solver layout (each row a contiguous run), and the substitution stages it
+// with bulk copies in either layout; FP32 writes the reciprocal to the
+// workspace at natural positions and the right-hand side in place (the
+// refinement reads that factor).  In cable mode
 // the system is rebuilt while staging (Section 1's implicit-Euler system):
 // d_i = s_i (1 + theta dt g_i) + sum of a over the edges at i (a = -u),
 // b_i = s_i V_i + s_i dt g_i (E - (1 - theta) V_i).
@@ -548,7 +566,8 @@ struct FactorMode {
     return r;
   }
   static constexpr bool kPacked = kPk;
-  static constexpr bool kNeedsBlk = false;
+  static constexpr bool kBF = sizeof(T) == 8;  // the factor in block order (FP64)
+  static constexpr bool kNeedsBlk = kBF;
   static constexpr int kPer = P;
   struct Args {
     const T* d;
@@ -567,18 +586,24 @@ struct FactorMode {
   // that more warps share an SM; FP32 with one piece per lane: two
   static constexpr int kStages = (sizeof(T) == 4 && P == 1) ? 2 : 1;
   static constexpr int kCslot = 0, kCx = 2 * G::kChunk * 2 * (int)sizeof(T);
-  static constexpr int kCacheBytes = kCx + 2 * G::kChunk * (int)sizeof(T);
+  static constexpr int kBar = kCx + 2 * G::kChunk * (int)sizeof(T);
+  static constexpr int kCacheBytes = kBar + (kBF ? 16 : 0);
   static constexpr int kWarpBytes = kStages * kStageBytes + kCacheBytes;
   static constexpr int kMinBlocks = kSmemPerSm / (kWarps * kWarpBytes);
-  static constexpr bool kBulk = false;
-  __device__ static void init_warp(unsigned char*, int) {}
+  // the factor block is staged by bulk copies (FP64 has one staging buffer)
+  static constexpr bool kBulk = kBF;
+  static_assert(!kBF || (kStages == 1 && kStageBytes % 16 == 0), "one staging buffer, 16-byte aligned");
+  using Bulk = BulkStage<kStageBytes + kBar>;
+  __device__ static void init_warp(unsigned char* wbase, int lane) {
+    if (kBulk) Bulk::init(wbase, lane);
+  }
+  __device__ static double2* factor_block(const DevPlan& Pl) { return static_cast<double2*>(Pl.ff4); }
 
-  // Section 1's implicit-Euler system: the membrane part of the diagonal,
-  // s (1 + theta dt g), and the right-hand side s (V + dt g (E - (1 - theta) V)),
-  // each in the fewest operations (theta = 1: s (V + dt E g))
-  // the diagonal less the compartment's own edge to its parent, s (1 + theta
-  // dt g) - a_own, in one FMA (a cell's root, which has no such edge, adds
-  // its u back: the same operations in both layouts)
+  // Section 1's implicit-Euler system, each part in the fewest operations:
+  // the diagonal less the compartment's own edge to its parent,
+  // s (1 + theta dt g) - a_own, in one FMA (a cell's root, which has no such
+  // edge, adds its u back: the same operations in both layouts), and the
+  // right-hand side s (V + dt g (E - (1 - theta) V)) (theta = 1: s (V + dt E g))
   __device__ static T cable_diag_edge(const Args& A, T si, T gi, T ui) {
     return fma(si, fma(A.theta * A.dt, gi, T(1)), -ui);
   }
@@ -604,9 +629,52 @@ struct FactorMode {
         if (q.len > 0 && q.pcomp >= 0 && !(loc >= 0 && loc < pv.n)) pre_set(m.xpre[h], A.x[q.pcomp]);
       }
     }
-    if (kPk) {
+    if constexpr (kBF) {
       int* tab = reinterpret_cast<int*>(buf + kTab);
       build_row_table<P>(m.L, lane, tab);
+      const int e = tab[kL];
+      const long long blk = kPk ? __shfl_sync(kFull, m.p[0].first, 0) : 0;
+      if (visit == 1) {
+        // the factor block (reciprocal pivot, eliminated right-hand side) over
+        // the first two arrays, u in the third
+        Bulk::template issue<1>(buf, lane, (unsigned)e * 16u, buf, factor_block(Pl) + m.blk);
+        if (kPk) {
+          stage_block(sb, A.u, blk, e, lane);
+        } else {
+          for_chunk_elements(m, n, lane, [&](int i, int, int row, long long g, bool) {
+            cp_async(&sb[nidx<P>(row, i)], A.u + g);
+          });
+        }
+        cp_commit();
+        return;
+      }
+      if (kReuse) {
+        // the stored reciprocal pivots from the block, u, and b rebuilt
+        const double* rp = reinterpret_cast<const double*>(factor_block(Pl) + m.blk);
+        if (kPk) {
+          for (int i = lane; i < e; i += 32) cp_async(&sd[i], rp + 2 * i);
+          stage_block(su, A.u, blk, e, lane);
+          for (int i = lane; i < e; i += 32) {
+            const long long g = blk + i;
+            const T vi = A.x[g];
+            sb[i] = A.rhs_from_V ? cable_rhs(A, A.s[g], A.g[g], vi) : vi;
+          }
+        } else {
+          for_chunk_elements(m, n, lane, [&](int i, int, int row, long long g, bool) {
+            const int q = nidx<P>(row, i);
+            cp_async(&sd[q], rp + 2 * (tab[row] + i));
+            cp_async(&su[q], A.u + g);
+            const T vi = A.x[g];
+            sb[q] = A.rhs_from_V ? cable_rhs(A, A.s[g], A.g[g], vi) : vi;
+          });
+        }
+        cp_commit();
+        return;
+      }
+    }
+    if (kPk) {
+      int* tab = reinterpret_cast<int*>(buf + kTab);
+      if constexpr (!kBF) build_row_table<P>(m.L, lane, tab);
       const long long blk = __shfl_sync(kFull, m.p[0].first, 0);
       const int e = tab[kL];
       if (kCable && visit == 0) {
@@ -676,10 +744,13 @@ struct FactorMode {
     T* cslot = reinterpret_cast<T*>(cache + kCslot);  // [2][kChunk][2] contributions
     T* cx = reinterpret_cast<T*>(cache + kCx);        // [2][kChunk] distal solutions
     T* slot = static_cast<T*>(Pl.cd);                 // [nb][2]
-    const Rows<kPk, P> rows{reinterpret_cast<const int*>(buf + kTab)};
+    const int* tab = reinterpret_cast<const int*>(buf + kTab);
+    const Rows<kPk, P> rows{tab};
+    if (kBulk && visit == 1) Bulk::wait(Pl, buf, lane);
     const int L = m.L;
     if (L == 0) return;
     const int me = P * lane;
+    double2* bf = kBF ? factor_block(Pl) + m.blk : nullptr;  // the chunk's factor block
     int first_row[P];  // each piece's distal row
 #pragma unroll
     for (int h = 0; h < P; ++h) first_row[h] = m.p[h].len > 0 ? L - m.p[h].len : kL;
@@ -725,8 +796,12 @@ struct FactorMode {
             if (r < first_row[h]) continue;
             const T uk = su[i + h];
             const T rr = kReuse ? sd[i + h] : rcp_solve(D[h]);
-            if (!kReuse) sd[i + h] = rr;
-            sb[i + h] = B[h];
+            if constexpr (kBF) {
+              bf[tab[r] + me + h] = make_double2(rr, B[h]);
+            } else {
+              if (!kReuse) sd[i + h] = rr;
+              sb[i + h] = B[h];
+            }
             const T f = uk * rr;
             const int i1 = rows.slot(r + 1, me + h);
             if (!kReuse) {
@@ -746,13 +821,14 @@ struct FactorMode {
           if (m.p[h].len == 0) continue;
           const T uk = su[i + h];
           const T rr = kReuse ? sd[i + h] : rcp_solve(D[h]);
-          if (!kReuse) sd[i + h] = rr;
+          if constexpr (kBF) bf[tab[L - 1] + me + h] = make_double2(rr, B[h]);  // a root's x is B rr
+          else if (!kReuse) sd[i + h] = rr;
           if (m.p[h].pcomp >= 0) {
             const T f = uk * rr;
-            sb[i + h] = B[h];
+            if constexpr (!kBF) sb[i + h] = B[h];
             c0v[h] = kReuse ? T(0) : (kCable ? f * uk + uk : f * uk);
             c1v[h] = f * B[h];
-          } else {
+          } else if constexpr (!kBF) {
             sb[i + h] = B[h] * rr;  // solve root
           }
         }
@@ -778,16 +854,37 @@ struct FactorMode {
         xp[h] = (loc >= 0 && loc < pv.n) ? cx[pv.which * G::kChunk + loc] : pre_get(m.xpre[h], T{});
       }
     }
+    if constexpr (kBF) {
+      // the staged block: (reciprocal pivot, eliminated right-hand side) per
+      // slot in block order, u in the third array; x goes over the pivot
+      const double2* fb = reinterpret_cast<const double2*>(buf);
+      double* sx = reinterpret_cast<double*>(buf);
 #pragma unroll
-    for (int r = kL - 1; r >= 0; --r) {
-      if (r < L) {
-        const int i = rows.slot(r, me);
+      for (int r = kL - 1; r >= 0; --r) {
+        if (r < L) {
+          const int i = rows.slot(r, me), q = tab[r] + me;
 #pragma unroll
-        for (int h = 0; h < P; ++h) {
-          if (r < first_row[h]) continue;
-          const T xi = (m.p[h].pcomp < 0 && r == L - 1) ? sb[i + h] : (sb[i + h] - su[i + h] * xp[h]) * sd[i + h];
-          sb[i + h] = xi;
-          xp[h] = xi;
+          for (int h = 0; h < P; ++h) {
+            if (r < first_row[h]) continue;
+            const double2 f = fb[q + h];
+            const T xi = (m.p[h].pcomp < 0 && r == L - 1) ? f.y * f.x : (f.y - sb[i + h] * xp[h]) * f.x;
+            sx[2 * (q + h)] = xi;
+            xp[h] = xi;
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = kL - 1; r >= 0; --r) {
+        if (r < L) {
+          const int i = rows.slot(r, me);
+#pragma unroll
+          for (int h = 0; h < P; ++h) {
+            if (r < first_row[h]) continue;
+            const T xi = (m.p[h].pcomp < 0 && r == L - 1) ? sb[i + h] : (sb[i + h] - su[i + h] * xp[h]) * sd[i + h];
+            sb[i + h] = xi;
+            xp[h] = xi;
+          }
         }
       }
     }
@@ -801,6 +898,21 @@ struct FactorMode {
     const T* sd = reinterpret_cast<const T*>(buf);
     const T* sb = sd + 2 * G::kSlots;
     T* fac = static_cast<T*>(Pl.fac);
+    if constexpr (kBF) {
+      // the elimination wrote its factor block directly; the substitution
+      // left x over each slot's pivot
+      if (visit == 0) return;
+      const double* sx = reinterpret_cast<const double*>(buf);
+      const int* tab = reinterpret_cast<const int*>(buf + kTab);
+      if (kPk) {
+        const long long blk = __shfl_sync(kFull, m.p[0].first, 0);
+        const int e = tab[kL];
+        for (int s = lane; s < e; s += 32) A.x[blk + s] = sx[2 * s];
+        return;
+      }
+      for_chunk_elements(m, n, lane, [&](int i, int, int row, long long g, bool) { A.x[g] = sx[2 * (tab[row] + i)]; });
+      return;
+    }
     if (kPk) {
       const int* tab = reinterpret_cast<const int*>(buf + kTab);
       const long long blk = __shfl_sync(kFull, m.p[0].first, 0);
