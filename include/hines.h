@@ -96,6 +96,14 @@ typedef struct {
   int32_t pack_whole;      /* the same fill for tasks of whole cells (cells of at most 4096
                               compartments; the other size class is the subtrees of larger cells):
                               0 as pack_compartments, a count, or -1 for Section 4's rule */
+  int32_t fp64_factor;     /* where the FP64 solves and cable steps keep their factor between the
+                              elimination and the substitution: 1 at natural positions (the
+                              reciprocal pivot in the workspace, the eliminated right-hand side in
+                              place), 2 in the chunks' block order (both as one 16-byte pair,
+                              staged back by bulk copies: faster on large batches, slower on
+                              latency-bound small ones), 0 (default) 2 for batches of at least
+                              50,331,648 compartments, else 1; other values HINES_ERR_INVALID_ARG.
+                              Results are the same bit for bit */
   int32_t reserved[1];     /* must be zero */
 } hines_plan_opts;
 

@@ -12,7 +12,9 @@ in which the elimination adds contributions into a compartment:
   layout, so that pieces share no memory sector, or into near-equal pieces);
 * Section 6's split at the level means, over the batch or per cell
   (``split_branches`` 1 / 2), whether ready branches of equal depth are taken
-  longest first, and re-rooting at the centres (solver layout only).
+  longest first, and re-rooting at the centres (solver layout only);
+* for the FP64 solves and cable steps, where the factor waits between the
+  sweeps (``fp64_factor``: natural positions or the chunks' block order).
 
 Which is fastest depends on the batch and on the solve, so ``tune_plan``
 times candidates on a synthetic diagonally dominant system of the same
@@ -47,6 +49,8 @@ SEARCH_SPACE = (
     ("sort_by_length", (False, True)),
 )
 SOLVER_LAYOUT_SPACE = (("reroot", (False, True)),)
+# where the FP64 solves keep their factor (natural positions or block order)
+FP64_SPACE = (("fp64_factor", (1, 2)),)
 SOLVES = ("compensated", "f64", "cable", "refine")
 
 # kept for callers that pass explicit candidate lists
@@ -141,7 +145,8 @@ def _time(fn, reps):
 
 def _search(ncomp, parent, solve, layout, reps, d, u, b):
     """Coordinate descent over the option space from the defaults."""
-    space = SEARCH_SPACE + (SOLVER_LAYOUT_SPACE if layout == "solver" else ())
+    space = SEARCH_SPACE + (SOLVER_LAYOUT_SPACE if layout == "solver" else ()) + (
+        FP64_SPACE if solve in ("f64", "cable") else ())
     best_opts, best_ms, best_plan = {}, None, None
     times = {}
     for name, values in space:

@@ -189,6 +189,7 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
   if (o.pack_compartments < -1) return HINES_ERR_INVALID_ARG;
   if (o.pieces_per_lane == 0) o.pieces_per_lane = 1;
   if (o.pieces_per_lane != 1 && o.pieces_per_lane != 2) return HINES_ERR_INVALID_ARG;
+  if (o.fp64_factor < 0 || o.fp64_factor > 2) return HINES_ERR_INVALID_ARG;
   hines_plan_t p = new (std::nothrow) hines_plan_s();
   if (!p) return HINES_ERR_OOM;
   int rc;
@@ -218,6 +219,10 @@ hines_status hines_plan_create(hines_plan_t* out, int32_t n_cells, const int32_t
     return (hines_status)rc;
   }
   p->host_only = o.host_only != 0;
+  // FP64 factors in block order where the batch fills default-size tasks
+  // (the planner's small-batch bound), or as asked
+  p->dev.fp64_blocks = o.fp64_factor == 2 || (o.fp64_factor == 0 && p->host.n_unknowns >=
+                                                                       hines::kMinTasks * hines::kTaskCompartments);
   if (!p->host_only) {
     if (cudaGetDevice(&p->device) != cudaSuccess) {
       cudaGetLastError();

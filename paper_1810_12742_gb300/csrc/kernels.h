@@ -53,6 +53,8 @@ struct DevPlan {
   const int64_t* pk_perm = nullptr;       // [n_packed] natural index of each solver-layout slot, -1 for padding
   const int64_t* pk_edge = nullptr;       // [n_packed] natural index of each slot's coupling (pk_perm unless re-rooted)
   int32_t grid[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // persistent grid size per kernel kind
+  int32_t grid_nf[4] = {1, 1, 1, 1};           // the same for the FP64 kinds keeping the factor at natural positions
+  int32_t fp64_blocks = 0;                     // 1: FP64 factors in block order (hines_plan_opts.fp64_factor)
   int32_t sms = 1;                             // multiprocessors of the plan's device
   int32_t per_lane = 2;                        // branch pieces per warp lane (the plan's lane mapping)
   int32_t grid_refine = 1;                     // persistent grid size of the refinement steps

@@ -553,7 +553,9 @@ struct CompMode {
 // solve of the same plan and matrix left in the workspace (the reciprocal
 // eliminated diagonal): only b is eliminated (the refinement's correction
 // solves; passive-cable steps after the first, the matrix being constant).
-template <typename T, bool kCable, bool kPk, int P, bool kReuse = false>
+// kBlk: FP64 keeps its factor in block order (else at natural positions, as
+// FP32 always does).
+template <typename T, bool kCable, bool kPk, int P, bool kReuse = false, bool kBlk = true>
 struct FactorMode {
   using G = Geo<P>;
   // the reciprocal eliminated diagonal: FP64 as rcp_t gives it; FP32 with one
@@ -566,7 +568,7 @@ struct FactorMode {
     return r;
   }
   static constexpr bool kPacked = kPk;
-  static constexpr bool kBF = sizeof(T) == 8;  // the factor in block order (FP64)
+  static constexpr bool kBF = kBlk && sizeof(T) == 8;  // the factor in block order (FP64)
   static constexpr bool kNeedsBlk = kBF;
   static constexpr int kPer = P;
   struct Args {
@@ -1380,6 +1382,13 @@ struct UnitKernels {
   using F32Reuse = FactorMode<float, false, false, PL, true>;
   using CableReuse = FactorMode<double, true, false, PL, true>;
   using PkCableReuse = FactorMode<double, true, true, PL, true>;
+  // the FP64 kinds with the factor at natural positions (small batches)
+  using F64N = FactorMode<double, false, false, PL, false, false>;
+  using CableN = FactorMode<double, true, false, PL, false, false>;
+  using PkF64N = FactorMode<double, false, true, PL, false, false>;
+  using PkCableN = FactorMode<double, true, true, PL, false, false>;
+  using CableReuseN = FactorMode<double, true, false, PL, true, false>;
+  using PkCableReuseN = FactorMode<double, true, true, PL, true, false>;
   using R32to2 = RefineMode<PL, 0, 0>;
   using R32to64 = RefineMode<PL, 0, 1>;
   using R2to2 = RefineMode<PL, 1, 0>;
@@ -1402,6 +1411,12 @@ struct UnitKernels {
     if (e == cudaSuccess) e = grid_of<R32to64>(P, &g_reuse);
     if (e == cudaSuccess) e = grid_of<R2to2>(P, &g_reuse);
     if (e == cudaSuccess) e = grid_of<R2to64>(P, &g_reuse);
+    if (e == cudaSuccess) e = grid_of<F64N>(P, &P.grid_nf[0]);
+    if (e == cudaSuccess) e = grid_of<CableN>(P, &P.grid_nf[1]);
+    if (e == cudaSuccess) e = grid_of<PkF64N>(P, &P.grid_nf[2]);
+    if (e == cudaSuccess) e = grid_of<PkCableN>(P, &P.grid_nf[3]);
+    if (e == cudaSuccess) e = grid_of<CableReuseN>(P, &g_reuse);
+    if (e == cudaSuccess) e = grid_of<PkCableReuseN>(P, &g_reuse);
     return e;
   }
 
@@ -1416,8 +1431,10 @@ struct UnitKernels {
     const float* b4 = static_cast<const float*>(c.b);
     float* x4 = static_cast<float*>(c.x);
     const double th = (double)c.theta;
+    const bool blk = P.fp64_blocks != 0;
     switch (c.op) {
       case UnitOp::F64:
+        if (!blk) return launch_phases<F64N>(P, {d8, u8, nullptr, nullptr, x8, 0.0, 0.0, 0.0, false}, P.grid_nf[0], s);
         return launch_phases<F64>(P, {d8, u8, nullptr, nullptr, x8, 0.0, 0.0, 0.0, false}, P.grid[0], s);
       case UnitOp::F32:
         return launch_phases<F32>(P, {d4, u4, nullptr, nullptr, x4, 0.f, 0.f, 0.f, false,
@@ -1427,18 +1444,27 @@ struct UnitKernels {
       case UnitOp::Comp:
         return launch_phases<Comp>(P, {d4, u4, b4, x8}, P.grid[3], s);
       case UnitOp::Cable:
+        if (!blk)
+          return launch_phases<CableN>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, c.rhs_from_V}, P.grid_nf[1], s);
         return launch_phases<Cable>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, c.rhs_from_V}, P.grid[2], s);
       case UnitOp::CableReuse:
+        if (!blk) return launch_phases<CableReuseN>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, true}, P.grid_nf[1], s);
         return launch_phases<CableReuse>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, true}, P.grid[2], s);
       case UnitOp::PkF64:
+        if (!blk)
+          return launch_phases<PkF64N>(P, {d8, u8, nullptr, nullptr, x8, 0.0, 0.0, 0.0, false}, P.grid_nf[2], s);
         return launch_phases<PkF64>(P, {d8, u8, nullptr, nullptr, x8, 0.0, 0.0, 0.0, false}, P.grid[4], s);
       case UnitOp::PkF32:
         return launch_phases<PkF32>(P, {d4, u4, nullptr, nullptr, x4, 0.f, 0.f, 0.f, false}, P.grid[5], s);
       case UnitOp::PkComp:
         return launch_phases<PkComp>(P, {d4, u4, b4, x8}, P.grid[6], s);
       case UnitOp::PkCable:
+        if (!blk)
+          return launch_phases<PkCableN>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, c.rhs_from_V}, P.grid_nf[3], s);
         return launch_phases<PkCable>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, c.rhs_from_V}, P.grid[7], s);
       case UnitOp::PkCableReuse:
+        if (!blk)
+          return launch_phases<PkCableReuseN>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, true}, P.grid_nf[3], s);
         return launch_phases<PkCableReuse>(P, {nullptr, u8, s8, g8, x8, c.dt, c.E, th, true}, P.grid[7], s);
       case UnitOp::Refine32to2:
         return launch_phases<R32to2>(P, {d4, u4, b4, c.rhs, c.rw, c.x, c.bcorr}, P.grid_refine, s);

@@ -53,7 +53,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("host_only", ctypes.c_int32), ("split_branches", ctypes.c_int32), ("pieces_per_lane", ctypes.c_int32),
                 ("sort_by_length", ctypes.c_int32), ("pack_compartments", ctypes.c_int32),
                 ("reroot", ctypes.c_int32), ("even_cuts", ctypes.c_int32), ("pack_whole", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("fp64_factor", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -155,17 +155,19 @@ class Plan:
     means) or 2 (the same at each cell's own level means).  even_cuts: cut
     long branches into near-equal pieces instead of at multiples of 8.
     pack_compartments / pack_whole: warp-task fill for the subtrees of large
-    cells / for whole cells (0: as pack_compartments)."""
+    cells / for whole cells (0: as pack_compartments).  fp64_factor: where FP64
+    solves and cable steps keep their factor (0 automatic, 1 natural positions,
+    2 block order)."""
 
     def __init__(self, ncomp, parent, split_branches: bool = False, host_only: bool = False, pieces_per_lane: int = 0,
                  sort_by_length: bool = False, pack_compartments: int = 0, reroot: bool = False,
-                 even_cuts: bool = False, pack_whole: int = 0):
+                 even_cuts: bool = False, pack_whole: int = 0, fp64_factor: int = 0):
         self._h = ctypes.c_void_p()
         _release_deferred()
         nc = np.ascontiguousarray(ncomp, np.int32)
         pa = np.ascontiguousarray(parent, np.int32)
         opts = PlanOpts(int(host_only), int(split_branches), int(pieces_per_lane), int(sort_by_length),
-                        int(pack_compartments), int(reroot), int(even_cuts), int(pack_whole))
+                        int(pack_compartments), int(reroot), int(even_cuts), int(pack_whole), int(fp64_factor))
         _check(lib().hines_plan_create(ctypes.byref(self._h), nc.size, _np_ptr(nc), _np_ptr(pa), ctypes.byref(opts)),
                "hines_plan_create")
         info = PlanInfo()
@@ -473,14 +475,14 @@ class HostPipeline:
         nc = np.ascontiguousarray(ncomp, np.int32)
         pa = np.ascontiguousarray(parent, np.int32)
         o = dict(host_only=False, split_branches=0, pieces_per_lane=0, sort_by_length=False, pack_compartments=0,
-                 reroot=False, even_cuts=False, pack_whole=0)
+                 reroot=False, even_cuts=False, pack_whole=0, fp64_factor=0)
         unknown = set(plan_options) - set(o)
         if unknown:
             raise TypeError(f"unknown plan options: {sorted(unknown)}")
         o.update(plan_options)
         opts = PlanOpts(int(o["host_only"]), int(o["split_branches"]), int(o["pieces_per_lane"]),
                         int(o["sort_by_length"]), int(o["pack_compartments"]), int(o["reroot"]),
-                        int(o["even_cuts"]), int(o["pack_whole"]))
+                        int(o["even_cuts"]), int(o["pack_whole"]), int(o["fp64_factor"]))
         _check(lib().hines_pipeline_create(ctypes.byref(self._h), nc.size, _np_ptr(nc), _np_ptr(pa), int(pieces),
                                            ctypes.byref(opts)), "hines_pipeline_create")
         npieces, n = ctypes.c_int32(), ctypes.c_int64()

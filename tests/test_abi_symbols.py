@@ -48,6 +48,9 @@ def test_argument_errors_without_gpu():
     opts.reserved[0] = 1
     assert L.hines_plan_create(ctypes.byref(h), 1, nc.ctypes.data_as(ctypes.c_void_p),
                                pa.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts)) == H.HINES_ERR_INVALID_ARG
+    opts = H.PlanOpts(1, 0, 0, 0, 0, 0, 0, 0, 3)  # FP64 factor placement: 0, 1 or 2 only
+    assert L.hines_plan_create(ctypes.byref(h), 1, nc.ctypes.data_as(ctypes.c_void_p),
+                               pa.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts)) == H.HINES_ERR_INVALID_ARG
     opts = H.PlanOpts(1, 0, 3)  # pieces per lane: 1 or 2 only
     assert L.hines_plan_create(ctypes.byref(h), 1, nc.ctypes.data_as(ctypes.c_void_p),
                                pa.ctypes.data_as(ctypes.c_void_p), ctypes.byref(opts)) == H.HINES_ERR_INVALID_ARG

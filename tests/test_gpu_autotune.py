@@ -79,7 +79,8 @@ def test_search_tunes_every_option_and_meets_the_gate(tmp_path, solve, layout):
     pop = uneven_subset()
     cache = str(tmp_path / "tune.json")
     plan, rep = T.tune_plan(pop["ncomp"], pop["parent"], solve, layout, reps=1, cache_path=cache)
-    space = T.SEARCH_SPACE + (T.SOLVER_LAYOUT_SPACE if layout == "solver" else ())
+    space = T.SEARCH_SPACE + (T.SOLVER_LAYOUT_SPACE if layout == "solver" else ()) + (
+        T.FP64_SPACE if solve in ("f64", "cable") else ())
     assert len(rep["ms"]) >= sum(len(v) for _, v in space) - len(space)
     assert set(rep["options"]) <= {k for k, _ in space}
     assert rep["ms"][__import__("json").dumps(rep["options"], sort_keys=True)] == min(rep["ms"].values())

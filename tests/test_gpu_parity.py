@@ -53,13 +53,22 @@ def zoo_batch(seed, sizes=(1, 2, 3, 17, 64, 65, 300, 1000)):
 @pytest.mark.parametrize("split", [0, 1, 2])
 @pytest.mark.parametrize("per_lane", [1, 2])
 def test_solve_f64_zoo(split, per_lane):
+    """Both places for the FP64 factor (natural positions, block order) match
+    the oracle and each other bit for bit, in both layouts."""
     ncomp, parent, c = zoo_batch(31)
-    plan = H.Plan(ncomp, parent, split_branches=split, pieces_per_lane=per_lane)
-    x = dev(c["b"])
-    H.solve(plan, dev(c["d"]), dev(c["u"]), x)
     ref = oracle.solve_batch(ncomp, parent, c["d"], c["u"], c["b"])
-    assert cell_rel_err(x.cpu().numpy(), ref, plan.offsets).max() <= TOL_F64
-    assert plan.status() == 0
+    xs, xps = [], []
+    for fp64_factor in (1, 2):
+        plan = H.Plan(ncomp, parent, split_branches=split, pieces_per_lane=per_lane, fp64_factor=fp64_factor)
+        x = dev(c["b"])
+        H.solve(plan, dev(c["d"]), dev(c["u"]), x)
+        assert cell_rel_err(x.cpu().numpy(), ref, plan.offsets).max() <= TOL_F64
+        pk = [H.pack(plan, dev(c[k])) for k in ("d", "u", "b")]
+        H.solve_packed(plan, *pk)
+        xps.append(H.unpack(plan, pk[2]))
+        xs.append(x)
+        assert plan.status() == 0
+    assert torch.equal(xs[0], xs[1]) and torch.equal(xps[0], xps[1]) and torch.equal(xs[0], xps[0])
 
 
 def test_inputs_not_modified_and_repeatable():

@@ -66,11 +66,13 @@ def test_thousand_steps_uneven_subset():
 
 
 @pytest.mark.parametrize("theta", [0, 1])
-def test_solver_layout_steps_equal_natural(theta):
+@pytest.mark.parametrize("fp64_factor", [1, 2])
+def test_solver_layout_steps_equal_natural(theta, fp64_factor):
     """hines_cable_step_packed / hines_cable_solve_packed give the natural-layout
-    results bit for bit; the graph stepper in the solver layout too."""
+    results bit for bit; the graph stepper in the solver layout too; for both
+    places of the factor."""
     w, pop = uneven_subset(24, 2)
-    plan = H.Plan(pop["ncomp"], pop["parent"])
+    plan = H.Plan(pop["ncomp"], pop["parent"], fp64_factor=fp64_factor)
     s, g, u = dev(pop["s"]), dev(pop["g"]), dev(pop["u"])
     V = dev(pop["V0"])
     pk = [H.pack(plan, t) for t in (s, g, u, V)]
@@ -123,12 +125,14 @@ def test_cable_steps_reusing_the_factor_equal_full_steps(theta):
 
 @pytest.mark.parametrize("theta", [0, 1])
 @pytest.mark.parametrize("layout", ["natural", "solver"])
-def test_cable_steps_reusing_the_factor_match_oracle(theta, layout):
+@pytest.mark.parametrize("fp64_factor", [1, 2])
+def test_cable_steps_reusing_the_factor_match_oracle(theta, layout, fp64_factor):
     """The factor-reuse variant against the oracle's own stepper directly (not
     only against the full steps): one full step, then steps that eliminate
-    only the rebuilt right-hand side with the stored factor."""
+    only the rebuilt right-hand side with the stored factor, wherever the plan
+    keeps it (natural positions or block order)."""
     w, pop = uneven_subset(20, 2)
-    plan = H.Plan(pop["ncomp"], pop["parent"])
+    plan = H.Plan(pop["ncomp"], pop["parent"], fp64_factor=fp64_factor)
     s, g, u = dev(pop["s"]), dev(pop["g"]), dev(pop["u"])
     K = 12
     if layout == "natural":
