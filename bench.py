@@ -291,7 +291,7 @@ def other_configs(torch, H, oracle, stream, max_over_ranks):
         r = {"skeel_cond_max": float(cond.max()),
              "compensated": _cell_err(xc, refs, pop["offsets"], cells),
              "fp32": _cell_err(xf.double().cpu().numpy(), refs, pop["offsets"], cells)}
-        for st in (1, 2):
+        for st in (1, 2, 3, 4):
             xr = H.solve_refine(plan, f32["d"], f32["u"], f32["b"], steps=st).cpu().numpy()
             r[f"fp32_refine_{st}"] = _cell_err(xr, refs, pop["offsets"], cells)
         sweep[f"{m:g}"] = r
