@@ -23,9 +23,12 @@
 // children are usually in the chunk just before it (elimination) and its
 // parents likewise (substitution): those values pass through a small shared
 // memory cache; other values go through global memory.  A chunk's inputs are
-// staged with cp.async into shared memory in the row layout of Section 5
-// (row r: the compartments r rows from each pair's distal start, one word per
-// piece), so that a lane reads its P values of a row as one word.
+// staged into shared memory in the row layout of Section 5 (row r: the
+// compartments r rows from each pair's distal start, one word per piece), so
+// that a lane reads its P values of a row as one word: gathered with cp.async
+// from the natural layout, or, where they are one contiguous block (the
+// solver layout, and the factor blocks the eliminations leave in block
+// order), by bulk copies one lane issues (BulkStage).
 #pragma once
 #include <cuda_runtime.h>
 
