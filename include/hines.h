@@ -481,6 +481,20 @@ hines_status hines_pipeline_status(hines_pipeline_t pipeline, int32_t *status_ou
 
 hines_status hines_pipeline_destroy(hines_pipeline_t pipeline);
 
+/*
+ * Check of the bounded device wait the solves use when they stage blocks with
+ * bulk copies (no paper counterpart).  One CTA on the current device sets up
+ * a shared-memory barrier that expects one arrival and polls it `polls`
+ * times (1 .. 65536); with arrive = 0 nothing ever arrives (no copy is
+ * issued), so the polls run out and the kernel records HINES_ERR_TIMEOUT in
+ * *status_out, as a solve records it in its plan's status word, and returns;
+ * with arrive = 1 the CTA makes the arrival itself and *status_out is
+ * HINES_OK.  *elapsed_ns (if not NULL) receives the time the polls took.
+ * Synchronous; allocates and frees a few bytes of device memory.  Nothing
+ * faults or hangs, and the context stays usable afterwards.
+ */
+hines_status hines_check_bounded_wait(int32_t polls, int32_t arrive, int32_t *status_out, int64_t *elapsed_ns);
+
 /* Static text of a status code. */
 const char *hines_status_string(int32_t status);
 

@@ -243,19 +243,24 @@ __device__ __forceinline__ F2 vset_hi(F2 v, float w) { return f2_make(f2_lo(v), 
 // ---- bulk staging -------------------------------------------------------------
 // Contiguous blocks are staged by one-dimensional bulk copies that one lane
 // issues, completing on a per-warp shared-memory barrier at byte kOff of the
-// warp's region (its phase parity in the word after it).  A mode with one
+// warp's region (then its phase parity and a failure flag).  A mode with one
 // staging buffer has at most one staging in flight, so one barrier does.
 template <int kOff>
 struct BulkStage {
   static_assert(kOff % 8 == 0, "barrier alignment");
-  static constexpr int kBytes = 16;           // barrier + parity word
-  static constexpr int kWaitPolls = 1 << 22;  // bounded wait (far beyond any real latency)
+  static constexpr int kBytes = 16;  // barrier, parity word, failure flag
+  // bounded wait: a poll that sees nothing suspends about 3.75 us on a GB300
+  // (hines_check_bounded_wait measures it), so about one second in all, far
+  // beyond any real copy latency
+  static constexpr int kWaitPolls = 1 << 18;
   __device__ static uint64_t* barrier(unsigned char* wbase) { return reinterpret_cast<uint64_t*>(wbase + kOff); }
+  __device__ static unsigned* words(unsigned char* wbase) { return reinterpret_cast<unsigned*>(barrier(wbase) + 1); }
   // once per warp, before its first task
   __device__ static void init(unsigned char* wbase, int lane) {
     if (lane == 0) {
       mbar_init(barrier(wbase));
-      reinterpret_cast<unsigned*>(barrier(wbase) + 1)[0] = 0u;
+      words(wbase)[0] = 0u;  // parity of the next phase
+      words(wbase)[1] = 0u;  // a wait of this warp has run out
     }
     __syncwarp();
   }
@@ -280,13 +285,19 @@ struct BulkStage {
     }
   }
   // every lane waits for the staged copies; a wait that runs out raises the
-  // plan's timeout status and goes on (no access leaves its buffer)
+  // plan's timeout status and goes on (no access leaves its buffer), and the
+  // warp's later waits poll only once, so that a failed launch ends within
+  // about a second instead of a second per chunk
   __device__ static void wait(const DevPlan& Pl, unsigned char* wbase, int lane) {
-    unsigned* ph = reinterpret_cast<unsigned*>(barrier(wbase) + 1);
-    const unsigned parity = *ph;
-    if (!mbar_wait(barrier(wbase), parity, kWaitPolls) && Pl.status) atomicCAS(Pl.status, 0, (int)HINES_ERR_TIMEOUT);
+    unsigned* w = words(wbase);
+    const unsigned parity = w[0];
+    const bool ok = mbar_wait(barrier(wbase), parity, w[1] ? 1 : kWaitPolls);
+    if (!ok && lane == 0 && Pl.status) atomicCAS(Pl.status, 0, (int)HINES_ERR_TIMEOUT);
     __syncwarp();
-    if (lane == 0) *ph = parity ^ 1u;
+    if (lane == 0) {
+      w[0] = parity ^ 1u;
+      if (!ok) w[1] = 1u;
+    }
     __syncwarp();
   }
 };

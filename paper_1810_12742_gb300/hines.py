@@ -39,7 +39,7 @@ EXPORTS = [
     "hines_cable_step_packed", "hines_cable_solve_packed", "hines_cable_step_reuse",
     "hines_pack_coupling", "hines_plan_export_reroot",
     "hines_pipeline_create", "hines_pipeline_info", "hines_pipeline_solve_compensated", "hines_pipeline_status",
-    "hines_pipeline_destroy",
+    "hines_pipeline_destroy", "hines_check_bounded_wait",
 ]
 
 
@@ -105,6 +105,7 @@ def lib():
             L.hines_pipeline_solve_compensated.argtypes = [vp, vp, vp, vp, vp, vp]
             L.hines_pipeline_status.argtypes = [vp, vp]
             L.hines_pipeline_destroy.argtypes = [vp]
+            L.hines_check_bounded_wait.argtypes = [i32, i32, vp, vp]
             L.hines_status_string.restype = ctypes.c_char_p
             for name in EXPORTS:
                 if name != "hines_status_string":
@@ -514,6 +515,15 @@ class HostPipeline:
             self.close()
         except Exception:
             pass
+
+
+def check_bounded_wait(polls: int, arrive: bool = False):
+    """hines_check_bounded_wait: (status, elapsed ns) of a barrier wait that
+    runs out after `polls` polls (arrive=False) or completes (arrive=True)."""
+    st, ns = ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().hines_check_bounded_wait(int(polls), int(bool(arrive)), ctypes.byref(st), ctypes.byref(ns)),
+           "hines_check_bounded_wait")
+    return st.value, ns.value
 
 
 def _hptr(t, dtype, n, name):

@@ -93,3 +93,11 @@ def test_pipeline_argument_errors_without_gpu():
     assert L.hines_pipeline_solve_compensated(None, None, None, None, None, None) == H.HINES_ERR_INVALID_ARG
     assert L.hines_pipeline_status(None, None) == H.HINES_ERR_INVALID_ARG
     assert L.hines_pipeline_destroy(None) == H.HINES_OK
+
+
+def test_bounded_wait_check_argument_errors_without_gpu():
+    L = H.lib()
+    st = ctypes.c_int32()
+    assert L.hines_check_bounded_wait(0, 0, ctypes.byref(st), None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_check_bounded_wait(1 << 17, 0, ctypes.byref(st), None) == H.HINES_ERR_INVALID_ARG
+    assert L.hines_check_bounded_wait(10, 0, None, None) == H.HINES_ERR_INVALID_ARG
