@@ -58,3 +58,26 @@ def test_traffic_record_follows_the_kernel_sources(monkeypatch):
     monkeypatch.setattr(_build, "unit_kernel_digest", lambda: "0" * 64)
     assert bench.traffic_record(key) is None
     assert bench.traffic_record("no such kernel") is None
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """bench.py --impl reference (the oracle on the host cores) prints one JSON
+    line with the keys the driver reads: the metric, value and unit of our arm,
+    impl, a cpu_baseline describing the run, and an end-to-end entry with no
+    transfers."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--cells", "16"], capture_output=True, text=True, cwd=root, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [x for x in out.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "compartments/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"]
