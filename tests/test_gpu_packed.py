@@ -40,6 +40,50 @@ def test_pack_unpack_round_trip(dtype):
     assert torch.equal(back, a)
 
 
+def _packed_reference(plan, host, coupling=False):
+    """Every slot from the plan's exported maps: the caller's value, zero in
+    padding; for couplings of a re-rooted plan, the value at the slot's edge."""
+    slots = plan.export_packed()
+    if coupling:
+        rr = plan.export_reroot()
+        inv = np.empty_like(rr["perm"])
+        inv[rr["perm"]] = np.arange(rr["perm"].size)
+        src = np.full(slots.size, -1, np.int64)
+        src[slots >= 0] = rr["edge"][inv[slots[slots >= 0]]]
+    else:
+        src = slots
+    ref = np.zeros(plan.n_packed, host.dtype)
+    ref[src >= 0] = host[src[src >= 0]]
+    return ref
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("opts", [dict(pieces_per_lane=2), dict(split_branches=1, even_cuts=True),
+                                  dict(reroot=True), dict(reroot=True, pieces_per_lane=2)],
+                         ids=["two_per_lane", "split_even", "rerooted", "rerooted_two_per_lane"])
+@pytest.mark.parametrize("batch", ["zoo", "uneven"])
+def test_pack_unpack_exact_for_every_plan_kind(dtype, opts, batch):
+    """Chunk-by-chunk permutations on every kind of plan: the packed array
+    equals the plan's slot map applied on the host (padding slots zero), the
+    couplings of a re-rooted plan follow its edge map, and unpacking gives
+    the caller's array back bit for bit."""
+    if batch == "zoo":
+        ncomp, parent, c = zoo_batch(43)
+        b = c["b"]
+    else:
+        pop = uneven_subset()
+        ncomp, parent, b = pop["ncomp"], pop["parent"], pop["b"]
+    plan = H.Plan(ncomp, parent, **opts)
+    a = dev(b, dtype)
+    host = a.cpu().numpy()
+    pk = H.pack(plan, a)
+    assert np.array_equal(pk.cpu().numpy(), _packed_reference(plan, host))
+    assert torch.equal(H.unpack(plan, pk), a)
+    pc = H.pack_coupling(plan, a).cpu().numpy()
+    assert np.array_equal(pc, _packed_reference(plan, host, coupling=bool(opts.get("reroot"))))
+    assert plan.status() == 0
+
+
 def _natural_and_packed(plan, d, u, b, mode):
     if mode == "f64":
         x = b.clone()
